@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: algebraic
+identities of Guo's incompressible equilibrium (Sec. 2.3, Eqs. 7-9), the
+transport coefficients of Eqs. 10 and 14 measured from decaying waves,
+closed-form flows (plane Poiseuille, uniform Darcy flow, Brinkman channel,
+Darcy pressure drop, pure conduction), the Rayleigh-Benard onset, the exact
+per-step mass balance, mirror symmetry, and published test vectors.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_12663_gb300 import workloads as W
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_published_vector():
+    """Counter-based noise generator: SplitMix64 against its published outputs."""
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    gamma = 0x9E3779B97F4A7C15
+    for k, v in enumerate(vals):
+        assert O.splitmix64((k * gamma) % 2**64) == v
+
+
+def test_equilibrium_values_at_rest():
+    """Eq. 7 at u = 0 with the reading sigma = 5/12, lambda = 1/3, gamma = 1/12."""
+    f = O.feq(1.0, 0.0, 0.0)
+    assert f[0] == pytest.approx(-4 * 5 / 12, rel=1e-15)
+    assert np.allclose(f[1:5], 1 / 3, rtol=1e-15)
+    assert np.allclose(f[5:9], 1 / 12, rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments(seed):
+    """Eqs. 7-9: sum feq = 0, sum e feq = u, sum e e feq = p I + u u, and
+    the moments of Eq. 9 recover (p, u) from feq."""
+    rng = np.random.default_rng(seed)
+    p, ux, uy = rng.normal(0, 1e-2), rng.normal(0, 3e-2), rng.normal(0, 3e-2)
+    f = O.feq(p, ux, uy)
+    assert abs(f.sum()) < 1e-16
+    assert f @ EX == pytest.approx(ux, abs=1e-17)
+    assert f @ EY == pytest.approx(uy, abs=1e-17)
+    assert f @ (EX * EX) == pytest.approx(p + ux * ux, abs=1e-16)
+    assert f @ (EY * EY) == pytest.approx(p + uy * uy, abs=1e-16)
+    assert f @ (EX * EY) == pytest.approx(ux * uy, abs=1e-17)
+    p2, ux2, uy2 = O.moments(f)
+    assert (p2, ux2, uy2) == pytest.approx((p, ux, uy), abs=1e-16)
+
+
+def _rand_cell(rng):
+    f = O.feq(rng.normal(0, 1e-2), rng.normal(0, 1e-2), rng.normal(0, 1e-2))
+    f = f + rng.normal(0, 1e-4, 9)
+    g = 0.25 * (0.5 + rng.normal(0, 0.1)) + rng.normal(0, 1e-3, 4)
+    return f, g
+
+
+@pytest.mark.parametrize("porous", [False, True])
+def test_collision_invariants(porous):
+    """Collision conserves sum_{i>=1} f (the mass of Guo's model, Eq. 9) and
+    T (Eq. 13); the flow momentum changes by exactly the applied force
+    (Eq. 17) in fluid cells."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        f, g = _rand_cell(rng)
+        drive = rng.normal(0, 1e-5, 2)
+        P = O.make_params(tau=rng.uniform(0.55, 1.5), tau_T=rng.uniform(0.55, 1.5),
+                          drive=tuple(drive), K=rng.uniform(0.05, 5.0))
+        fs, gs = O.collide(P, porous, f, g)
+        assert fs[1:].sum() == pytest.approx(f[1:].sum(), abs=1e-16)
+        assert gs.sum() == pytest.approx(g.sum(), abs=1e-15)
+        _, ux, uy = O.moments(f)
+        jx, jy = fs @ EX, fs @ EY
+        if not porous:
+            assert jx == pytest.approx(ux + drive[0], abs=1e-16)
+            assert jy == pytest.approx(uy + drive[1], abs=1e-16)
+        else:
+            # Darcy drag of Eq. 4 taken at the mid-step momentum
+            nu = (2 * P.tau - 1) / 6
+            umx = (ux + 0.5 * drive[0]) / (1 + nu / (2 * P.K))
+            assert jx == pytest.approx(ux + drive[0] - nu / P.K * umx, abs=1e-16)
+
+
+def test_buoyancy_force_direction_and_size():
+    """Eq. 17 (generalised to every axis link): the force adds
+    -g beta (T - T0) g_hat of momentum and no mass; it lives on i = 1..4."""
+    f, g = _rand_cell(np.random.default_rng(9))
+    T = g.sum()
+    for gdir in [(0.0, -1.0), (-1.0, 0.0), (0.6, -0.8)]:
+        P0 = O.make_params(tau=0.9, tau_T=0.7, T0=0.3)
+        P1 = O.make_params(tau=0.9, tau_T=0.7, T0=0.3, g_beta=1e-3, g_dir=gdir)
+        d = O.collide(P1, False, f, g)[0] - O.collide(P0, False, f, g)[0]
+        assert abs(d.sum()) < 1e-18
+        assert np.all(d[5:] == 0) and d[0] == 0
+        assert d @ EX == pytest.approx(-1e-3 * (T - 0.3) * gdir[0], rel=1e-12, abs=1e-20)
+        assert d @ EY == pytest.approx(-1e-3 * (T - 0.3) * gdir[1], rel=1e-12, abs=1e-20)
+        # hot fluid (T > T0) is pushed against gravity
+        assert (d @ EX) * gdir[0] + (d @ EY) * gdir[1] < 0
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.3])
+def test_shear_wave_viscosity(tau):
+    """Eq. 10: a decaying shear wave in a periodic box gives nu = (2 tau - 1)/6."""
+    n = 64
+    k = 2 * math.pi / n
+    m = np.zeros((n, 1), np.uint8)
+    s = O.State(O.mask_geom(1, n, 1, 1), O.make_params(tau=tau), m)
+    for c in range(n):
+        s.f[:, c] = O.feq(0.0, 1e-4 * math.sin(k * c), 0.0)
+    s.run(100)
+    a1 = np.abs(s.fields()[0][0]).max()
+    s.run(400)
+    a2 = np.abs(s.fields()[0][0]).max()
+    nu = -math.log(a2 / a1) / (400 * k * k)
+    assert nu == pytest.approx((2 * tau - 1) / 6, rel=5e-3)
+
+
+@pytest.mark.parametrize("tau_T", [0.55, 0.8, 1.2])
+def test_diffusion_wave_diffusivity(tau_T):
+    """Eq. 14: a decaying temperature wave at rest gives theta = (2 tau_T - 1)/4."""
+    n = 64
+    k = 2 * math.pi / n
+    m = np.zeros((1, n), np.uint8)
+    s = O.State(O.mask_geom(n, 1, 1, 1), O.make_params(tau=0.8, tau_T=tau_T), m)
+    s.T[:] = 0.25 * (1.0 + 0.1 * np.sin(k * np.arange(n)))[None, :]
+    s.run(100)
+    a1 = np.abs(s.fields()[2] - 1).max()
+    s.run(400)
+    a2 = np.abs(s.fields()[2] - 1).max()
+    theta = -math.log(a2 / a1) / (400 * k * k)
+    assert theta == pytest.approx((2 * tau_T - 1) / 4, rel=5e-3)
+
+
+def _channel_profile(H, tau, G, porous=False, K=1.0):
+    m, d = W.channel(2, H, porous=porous)
+    s = O.State(O.mask_geom(d["nx"], d["ny"], 1, 0),
+                O.make_params(tau=tau, drive=(G, 0.0), K=K), m)
+    nu = (2 * tau - 1) / 6
+    s.run(int(8 * H * H / nu) if not porous else int(40 * K / nu + 8 * min(H * H, 50 * K) / nu))
+    u = s.fields()[0][0].reshape(d["ny"], d["nx"])[1:-1, 0]
+    return s, u, nu
+
+
+def test_plane_poiseuille_second_order():
+    """Halfway bounce-back + BGK + forcing: steady plane Poiseuille flow
+    u = G/(2 nu) (y - 1/2)(H + 1/2 - y) with second-order convergence."""
+    errs = []
+    for H in (8, 16, 32):
+        _, u, nu = _channel_profile(H, 0.8, 1e-6)
+        y = np.arange(1, H + 1)
+        ex = 1e-6 / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+        errs.append(np.abs(u - ex).max() / ex.max())
+    assert errs[-1] < 1e-3
+    for a, b in zip(errs, errs[1:]):
+        assert 3.5 < a / b < 4.5
+
+
+def test_wall_shear_stress_channel():
+    """Sec. 3.6 WSS from the non-equilibrium stress: in Poiseuille flow the
+    shear stress half a cell from the wall is G (H - 1) / 2 exactly."""
+    H, G = 32, 1e-6
+    s, _, _ = _channel_profile(H, 0.8, G)
+    o = s.observe()
+    assert o["wss_iris"] == pytest.approx(G * (H - 1) / 2, rel=1e-9)
+    assert o["wss_cornea"] == pytest.approx(G * (H - 1) / 2, rel=1e-9)
+    assert o["n_iris"] == 2 and o["n_cornea"] == 2
+
+
+def test_uniform_porous_box_darcy_velocity():
+    """Eq. 4 in a uniform periodic porous box driven by G: u = K G / nu to
+    round-off."""
+    m, d = W.porous_box(4, 4)
+    for K in (0.05, 0.5, 5.0):
+        P = O.make_params(tau=0.8, drive=(1e-5, -2e-6), K=K)
+        s = O.State(O.mask_geom(4, 4, 1, 1), P, m)
+        s.run(400 + int(40 * K / 0.1))
+        u = s.fields()[0]
+        assert np.allclose(u[0], K * 1e-5 / 0.1, rtol=1e-12)
+        assert np.allclose(u[1], -K * 2e-6 / 0.1, rtol=1e-12)
+
+
+def test_brinkman_channel_second_order():
+    """Porous channel (Brinkman with effective viscosity nu):
+    u = (G K / nu)[1 - cosh((y - y_c)/sqrt K) / cosh(H / (2 sqrt K))],
+    converging as the lattice resolves sqrt K (H / sqrt K fixed)."""
+    errs = []
+    for H in (16, 32):
+        K = (H / 8.0) ** 2
+        _, u, nu = _channel_profile(H, 0.8, 1e-6, porous=True, K=K)
+        y = np.arange(1, H + 1)
+        yc, sk = (H + 1) / 2, math.sqrt(K)
+        ex = 1e-6 * K / nu * (1 - np.cosh((y - yc) / sk) / np.cosh(H / (2 * sk)))
+        errs.append(np.abs(u - ex).max() / ex.max())
+    assert errs[0] < 6e-3 and errs[1] < errs[0] / 2.5
+
+
+@pytest.mark.parametrize("K", [0.05, 0.5, 2.0])
+def test_darcy_pressure_drop_and_iop(K):
+    """Inlet -> fluid -> porous block (length L) -> fluid -> outlet, periodic
+    across: the drop over the block is nu Q L / K (mu Q L / (K A) per unit
+    width), the interior slope is -(nu/K) Q, outflow equals inflow, and IOP
+    (mean p over fluid cells) equals the upstream share of the drop."""
+    n_in, L, n_out, ny, u, tau = 8, 32, 8, 2, 1e-4, 0.8
+    nu = (2 * tau - 1) / 6
+    m, d = W.darcy_column(n_in, L, n_out, ny)
+    g = O.mask_geom(d["nx"], d["ny"], 0, 1, d["inlet_dir"], d["inlet_profile"])
+    s = O.State(g, O.make_params(tau=tau, u_in_max=u, K=K), m)
+    s.run(4000 + int(3000 / K))
+    p = s.fields()[1].reshape(ny, -1)[0]
+    x0, x1 = 1 + n_in, 1 + n_in + L
+    dp = nu * u * L / K
+    assert p[x0 - 1] - p[x1] == pytest.approx(dp, rel=1e-9)
+    slope = np.diff(p[x0 + 2:x1 - 2])
+    assert np.allclose(slope, -nu / K * u, rtol=1e-9)
+    o = s.observe()
+    assert o["iop"] == pytest.approx(dp * n_in / (n_in + n_out), rel=1e-9)
+    qi, qo = s.step()
+    assert qi == pytest.approx(u * ny, rel=1e-12)
+    assert qo == pytest.approx(qi, rel=1e-9)
+
+
+def test_pure_conduction_linear_profile():
+    """Eqs. 11-14 with anti-bounce-back Dirichlet walls at rest: the steady
+    temperature is linear between the halfway walls, to round-off."""
+    H = 16
+    m, d = W.channel(2, H)
+    P = O.make_params(tau=0.8, tau_T=0.7, T_hot=1.0, T_cold=0.0, T0=0.5)
+    s = O.State(O.mask_geom(2, H + 2, 1, 0), P, m)
+    s.run(30000)
+    u, _, T = s.fields()
+    Ty = T.reshape(H + 2, 2)[1:-1, 0]
+    y = np.arange(1, H + 1)
+    assert np.abs(Ty - (1.0 - (y - 0.5) / H)).max() < 1e-12
+    assert np.abs(u).max() == 0.0
+
+
+def _rb_growth(Ra, H=16, nx=32, tau=0.8):
+    m, d = W.channel(nx, H)
+    tT = W.tau_T_for_Pr(tau, 1.0)
+    gb = W.ra_to_gbeta(Ra, tau, tT, 1.0, H)
+    P = O.make_params(tau=tau, tau_T=tT, g_beta=gb, g_dir=(0, -1), T_hot=1.0,
+                      T_cold=0.0, T0=0.5, noise_amp=1e-3, seed=7)
+    s = O.State(O.mask_geom(nx, H + 2, 1, 0), P, m)
+    s.run(4000)
+    e1 = float((s.fields()[0][0] ** 2).sum())
+    s.run(8000)
+    e2 = float((s.fields()[0][0] ** 2).sum())
+    return e2 / e1
+
+
+def test_rayleigh_benard_onset():
+    """Boussinesq coupling (Eqs. 5, 15-17): a fluid layer heated from below
+    between rigid walls stays conductive below the textbook critical
+    Rayleigh number 1708 and convects above it."""
+    assert _rb_growth(1500.0) < 1e-3
+    assert _rb_growth(2000.0) > 10.0
+
+
+def _eye(nx=160, ny=80, **kw):
+    m, g = O.eye_mask(nx, ny, kw.pop("angle_deg", 45.0))
+    pp = W.eye_params(ny, tau=0.8, Ra=1e4, K_tm=0.05)
+    pp.update(kw)
+    return m, g, O.make_params(**pp)
+
+
+def test_mass_balance_every_step():
+    """Guo's model conserves M = sum_{i>=1} f in collision, so each step
+    M(n+1) - M(n) = q_in(n) - q_out(n) up to round-off."""
+    m, g, P = _eye()
+    s = O.State(g, P, m)
+    s.run(300)
+    for _ in range(10):
+        m0 = s.observe()["mass"]
+        qi, qo = s.step()
+        m1 = s.observe()["mass"]
+        assert abs((m1 - m0) - (qi - qo)) <= 1e-13 * np.abs(s.f[1:]).sum()
+    assert qi == pytest.approx(0.005 * 4 * (0.4375 * 2 + 0.9375 * 2) / 4, rel=1e-12)
+
+
+def test_rest_state_stays_at_rest():
+    """No inflow, no temperature difference, no noise: u = 0 and p = p_out
+    exactly, whatever the gravity direction."""
+    for gdir in (W.UPRIGHT, W.SUPINE):
+        m, g, P = _eye(u_in_max=0.0, T_hot=0.5, T_cold=0.5, T_in=0.5, T0=0.5,
+                       noise_amp=0.0, g_dir=gdir)
+        s = O.State(g, P, m)
+        s.run(300)
+        u, p, _ = s.fields()
+        assert np.abs(u).max() == 0.0 and np.abs(p).max() == 0.0
+
+
+def test_supine_eye_mirror_symmetry():
+    """Mirror-symmetric eye, gravity along the optical axis, no noise: u_x is
+    odd and u_y, p, T are even about the mid-line (the two mirror vortices of
+    the up-facing eye)."""
+    m, g, P = _eye(g_dir=W.SUPINE, noise_amp=0.0)
+    s = O.State(g, P, m)
+    s.run(1500)
+    u, p, T = s.fields()
+    ux, uy = u[0].reshape(80, 160), u[1].reshape(80, 160)
+    p, T = p.reshape(80, 160), T.reshape(80, 160)
+    assert np.abs(ux + ux[:, ::-1]).max() < 1e-12 * np.abs(ux).max()
+    assert np.abs(uy - uy[:, ::-1]).max() < 1e-12 * np.abs(uy).max()
+    assert np.abs(p - p[:, ::-1]).max() < 1e-12 * np.abs(p).max()
+    assert np.abs(T - T[:, ::-1]).max() < 1e-12
+
+
+@pytest.mark.parametrize("angle", [20.0, 30.0, 45.0])
+def test_eye_geometry(angle):
+    """The analytic eye: mirror-symmetric, one inlet gap, two TM blocks with
+    outlets behind, and a cornea arc whose sagitta a tan(alpha/2) sets the
+    chamber angle alpha."""
+    nx, ny = 320, 160
+    m, g = O.eye_mask(nx, ny, angle)
+    assert np.array_equal(m, m[:, ::-1])
+    assert (m == O.INLET).sum() == g.inlet_width == 8
+    assert (m == O.OUTLET).sum() == 2 * 20
+    band = 16
+    xa = 12 + 2
+    a = nx / 2 - xa
+    h = a * math.tan(math.radians(angle) / 2)
+    fluid_rows = np.where((m == O.FLUID).any(axis=1))[0]
+    assert fluid_rows.min() == band
+    assert abs((fluid_rows.max() + 0.5) - (band - 0.5 + h)) <= 1.0
+    cols = np.where((m == O.FLUID).any(axis=0))[0]
+    assert cols.min() >= xa and cols.max() <= nx - 1 - xa
+    assert abs((cols.max() - cols.min() + 1) - 2 * a) <= 2.0
