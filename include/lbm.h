@@ -1,0 +1,262 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) coupled lattice Boltzmann solver for
+ * aqueous-humor flow in the anterior chamber (arXiv 2102.12663).
+ *
+ * Model (Sec. 2.3 of the paper): Guo's incompressible D2Q9 BGK model for flow
+ * (Eqs. 6-10) with the Boussinesq buoyancy force of Eqs. 15-17, a D2Q4 BGK
+ * model for heat convection and diffusion (Eqs. 11-14), Darcy resistance of the
+ * trabecular meshwork (Eq. 4) in porous cells, halfway bounce-back walls
+ * (Bouzidi's scheme at q = 1/2), a velocity inlet at the ciliary body, a
+ * fixed-pressure outlet behind the meshwork, and fixed-temperature walls on
+ * the cornea (Gamma_1) and iris/lens (Gamma_2).  Observables: IOP (Sec. 2.3,
+ * "the pressure in AC is just IOP"; Sec. 3.1), inflow and outflow rates
+ * (Sec. 3.1, Fig. 2), peak speed (Tab. 3) and the mean cornea and iris wall
+ * shear stress (Sec. 3.6, Tabs. 8-9).
+ *
+ * Conventions for every entry point:
+ *  - All quantities are lattice units (c = dx = dt = 1) unless a name ends in
+ *    _pa (pascal) or _m / _s (SI).  Cell (x, y) has flat index y*nx + x; x runs
+ *    across the chamber, y along the optical axis.
+ *  - D2Q9 velocities e_0..e_8 = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+ *    (-1,-1) (1,-1); the D2Q4 heat lattice uses e_1..e_4.
+ *  - Every call returns an lbm_status; nothing throws across the ABI.  On an
+ *    error, lbm_last_error() returns a message for the calling thread.
+ *  - Device memory belongs to the caller: each object lives inside one device
+ *    buffer that the caller allocates (lbm_*_bytes gives the size), keeps
+ *    alive until the object is destroyed, and frees afterwards.  The library
+ *    itself calls no device allocator.  Host-side bookkeeping uses malloc.
+ *  - Work is queued on the caller's CUDA stream (a cudaStream_t passed as
+ *    void*, 0 = legacy default stream); calls that return data to the host
+ *    synchronise that stream.
+ *  - Handles are not thread-safe: one thread drives a handle at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,         /* invalid argument; nothing was changed */
+    LBM_ENOMEM = 2,         /* caller buffer too small or misaligned */
+    LBM_ECUDA = 3,          /* a CUDA runtime call failed */
+    LBM_ENOTCONVERGED = 4,  /* lbm_run_to_steady hit max_steps */
+    LBM_EUNSTABLE = 5,      /* NaN detected in the observables */
+    LBM_EBUSY = 6           /* object in use (batch slot taken, batch full) */
+} lbm_status;
+
+/* Storage precision of the populations.  Arithmetic is FP64 for LBM_F64 and
+ * FP32 otherwise; reductions always accumulate in FP64.  The 16-bit forms
+ * store the flow populations of Guo's model (which vanish at rest, so they are
+ * already deviations from the rest weights) scaled by a power of two, and the
+ * heat populations as deviations from T0/4. */
+typedef enum lbm_precision {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F16DEV = 2,
+    LBM_BF16DEV = 3
+} lbm_precision;
+
+typedef enum lbm_geom_kind {
+    LBM_GEOM_EYE = 0,  /* the library's analytic eye (see lbm_build_mask) */
+    LBM_GEOM_MASK = 1  /* caller-supplied cell-type mask */
+} lbm_geom_kind;
+
+/* Cell types of a mask (Sec. 2.1 regions: Omega_1 fluid, Omega_3 porous TM,
+ * Gamma_1 cornea, Gamma_2 iris/lens, inlet at the ciliary body, outlet behind
+ * the TM).  Walls are solid; inlet and outlet cells are boundary cells that
+ * are never updated. */
+typedef enum lbm_cell_type {
+    LBM_CELL_FLUID = 0,
+    LBM_CELL_POROUS = 1,
+    LBM_CELL_COLD = 2,       /* cornea: no-slip, T = T_cold */
+    LBM_CELL_HOT = 3,        /* iris / lens: no-slip, T = T_hot */
+    LBM_CELL_ADIABATIC = 4,  /* sclera and outer box: no-slip, zero heat flux */
+    LBM_CELL_INLET = 5,      /* prescribed inflow, T = T_in */
+    LBM_CELL_OUTLET = 6      /* p = p_out, zero temperature gradient */
+} lbm_cell_type;
+
+/* Geometry of one problem (Sec. 2.1, Tab. 1).
+ * EYE: nx, ny, chamber_angle_deg and optionally band_cells (iris/lens band
+ *      height), inlet_cells (ciliary inlet width), tm_w, tm_h (trabecular
+ *      meshwork block); 0 selects the default scaled from the 160 x 80 eye
+ *      (band ny/10, inlet 4, TM 6 x 10 cells per 160 columns).
+ * MASK: nx, ny, host_mask (ny*nx lbm_cell_type bytes, read during
+ *      lbm_create_domain only), periodic_x / periodic_y (wrap-around edges;
+ *      every non-periodic edge must hold no fluid or porous cell), and the
+ *      inflow: lattice direction (inlet_dir_x, inlet_dir_y), inlet_profile 0
+ *      (plug) or 1 (parabolic 4 s (1 - s) over inlet_width cells starting at
+ *      inlet_lo, counted along the axis across the inflow). */
+typedef struct lbm_geometry_desc {
+    int32_t nx, ny;
+    int32_t kind;
+    int32_t band_cells, inlet_cells, tm_w, tm_h;
+    int32_t periodic_x, periodic_y;
+    int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
+    double chamber_angle_deg;
+    const uint8_t* host_mask;
+} lbm_geometry_desc;
+
+/* Summary of a built mask (lbm_build_mask). */
+typedef struct lbm_geometry_info {
+    int64_t n_cells, n_active, n_fluid, n_porous, n_inlet, n_outlet;
+    int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
+    int32_t eye_normals;     /* 1: analytic cornea / iris wall normals */
+    double arc_xc, arc_yc;   /* centre of the cornea arc (EYE) */
+} lbm_geometry_info;
+
+/* Physical parameters (lattice units).  May change between steps.
+ *  tau, tau_T   relaxation times, nu = (2 tau - 1)/6 (Eq. 10),
+ *               theta = (2 tau_T - 1)/4 (Eq. 14); both must exceed 1/2.
+ *  g_beta       gravity times thermal expansion (Eq. 17); g_dir its unit
+ *               direction (upright eye (-1, 0), supine (0, -1)).
+ *  T_cold, T_hot, T_in  cornea, iris/lens and inflow temperatures;
+ *  T0           reference temperature of the Boussinesq term (Eq. 5).
+ *  u_in_max     peak inflow speed of the inlet profile.
+ *  K_tm         TM permeability in cells^2 (> 0); porosity is carried for
+ *               reporting only (Tab. 5 labels).
+ *  p_out        outlet pressure (Schlemm's canal).
+ *  drive        uniform body force (test flows; 0 for the eye).
+ *  noise_amp, seed  amplitude and seed of the initial temperature noise.
+ *  dx_m, dt_s, rho0, p_sc_pa  unit conversion for the *_pa outputs:
+ *               IOP_pa = p_sc_pa + rho0 (dx/dt)^2 (iop - p_out). */
+typedef struct lbm_params {
+    double tau, tau_T;
+    double g_beta;
+    double g_dir[2];
+    double T_cold, T_hot, T0, T_in;
+    double u_in_max;
+    double K_tm, porosity;
+    double p_out;
+    double drive[2];
+    double noise_amp;
+    uint64_t seed;
+    double dx_m, dt_s, rho0, p_sc_pa;
+} lbm_params;
+
+/* Observables of the state at time `step` (pre-collision populations).
+ * q_in / q_out are the boundary fluxes of the step step -> step+1. */
+typedef struct lbm_observables {
+    int64_t step;
+    double iop, iop_pa;           /* mean pressure over fluid cells */
+    double q_in, q_out;           /* inflow / outflow per step */
+    double mass;                  /* sum of f_1..f_8 over active cells */
+    double peak_speed;            /* max |u| over active cells */
+    double wss_cornea, wss_iris;  /* mean wall shear stress, lattice units */
+    double wss_cornea_pa, wss_iris_pa;
+    double residual;              /* max |u - u_snapshot|, -1 without snapshot */
+    int64_t n_fluid, n_cornea, n_iris;
+    int32_t nan_flag;             /* non-zero if any pressure was NaN */
+    int32_t reserved;
+} lbm_observables;
+
+/* Launch shape of the fused step kernel: tiles of tile_w x (block_rows *
+ * rows_per_thread) cells, one thread per column and row group;
+ * blocks_per_sm > 0 selects a persistent grid of that many blocks per SM,
+ * 0 one block per tile.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
+ * <= 1024, tile area >= 128 cells. */
+typedef struct lbm_launch {
+    int32_t tile_w, block_rows, rows_per_thread, blocks_per_sm;
+} lbm_launch;
+
+typedef struct lbm_domain lbm_domain;
+typedef struct lbm_batch lbm_batch;
+
+/* ---- geometry (host only; no GPU needed) ---------------------------------*/
+
+/* Build the cell-type mask of a geometry into host_out (ny*nx bytes) and
+ * summarise it in *info (either may be NULL).  The analytic eye: solid outer
+ * ring; iris/lens band y < band_cells between the two chamber-angle points;
+ * ciliary inlet = the band's top row over a centred gap; cornea = circular arc
+ * over the chord y = band - 1/2 whose sagitta a tan(angle/2) sets the chamber
+ * angle (Tab. 1, Sec. 3.5); a porous TM block at each angle point with a
+ * one-cell outlet column behind it.  EINVAL if the geometry does not fit. */
+lbm_status lbm_build_mask(const lbm_geometry_desc* desc, uint8_t* host_out,
+                          lbm_geometry_info* info);
+
+/* ---- one problem ---------------------------------------------------------*/
+
+/* Bytes of device memory a domain needs (0 if desc is invalid). */
+size_t lbm_domain_bytes(const lbm_geometry_desc* desc, int32_t precision);
+
+/* Create a domain inside dev_buf (>= lbm_domain_bytes, 256-byte aligned,
+ * caller-owned, must outlive the domain).  Builds and uploads the mask on
+ * `stream`.  The state is initialised by the first lbm_set_params. */
+lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t precision,
+                             void* dev_buf, size_t bytes, void* stream,
+                             lbm_domain** out);
+
+/* Validate and install parameters (Tab. 2 quantities in lattice units).
+ * EINVAL if tau or tau_T <= 1/2, K_tm <= 0, |g_dir| not 1 while g_beta != 0,
+ * or any value is not finite.  The first call also resets the state. */
+lbm_status lbm_set_params(lbm_domain* dom, const lbm_params* params);
+
+/* Reset to t = 0: f_i = f_i^eq(p_out, u = 0) (Eq. 7) and T_i = (T0 + n)/4 in
+ * active cells, n = noise_amp (2 U - 1) with U the top 53 bits of
+ * SplitMix64(seed XOR cell index) / 2^53.  Drops the velocity snapshot. */
+lbm_status lbm_reset_state(lbm_domain* dom);
+
+/* Advance nsteps >= 0 time steps (Eq. 6 and Eq. 11 with all boundary rules),
+ * asynchronously on the domain's stream. */
+lbm_status lbm_step(lbm_domain* dom, int64_t nsteps);
+
+/* Step until the largest change of |u| over check_every steps falls below tol
+ * (the steady criterion max |du| < tol per check_every steps), or max_steps
+ * have been taken.  *steps_out (may be NULL) receives the steps taken.
+ * Returns ENOTCONVERGED at the cap and EUNSTABLE on a NaN.  Synchronises the
+ * stream once per check. */
+lbm_status lbm_run_to_steady(lbm_domain* dom, double tol, int32_t check_every,
+                             int64_t max_steps, int64_t* steps_out);
+
+/* Reduce the observables of the current state (FP64 accumulation) and copy
+ * them to *out; synchronises the stream. */
+lbm_status lbm_read_observables(lbm_domain* dom, lbm_observables* out);
+
+/* Write the macroscopic fields of the current state to caller device buffers
+ * (any may be NULL): dev_u = 2*nx*ny doubles (u_x plane then u_y), dev_p and
+ * dev_T = nx*ny doubles each (Eq. 9, Eq. 13); zero outside active cells. */
+lbm_status lbm_read_field(lbm_domain* dom, double* dev_u, double* dev_p, double* dev_T);
+
+/* Copy the populations of the current state, in natural order, to caller
+ * device buffers: dev_f = 9*nx*ny doubles (plane i holds f_i), dev_g = 4*nx*ny
+ * doubles (T_1..T_4); zero outside active cells. */
+lbm_status lbm_read_populations(lbm_domain* dom, double* dev_f, double* dev_g);
+
+/* Overwrite the populations of active cells from caller device buffers laid
+ * out as in lbm_read_populations (rounded to the storage precision). */
+lbm_status lbm_write_populations(lbm_domain* dom, const double* dev_f, const double* dev_g);
+
+/* Checkpoint: lbm_state_bytes host bytes hold the raw stored populations, the
+ * step counter and the parameters; save synchronises the stream. */
+size_t lbm_state_bytes(const lbm_domain* dom);
+lbm_status lbm_save_state(lbm_domain* dom, void* host_buf, size_t bytes);
+lbm_status lbm_load_state(lbm_domain* dom, const void* host_buf, size_t bytes);
+
+/* Launch shape of this domain's kernels (see lbm_launch). */
+lbm_status lbm_set_launch(lbm_domain* dom, const lbm_launch* launch);
+lbm_status lbm_get_launch(const lbm_domain* dom, lbm_launch* launch);
+
+/* Time step counter, geometry summary, number of tiles of the launch shape. */
+int64_t lbm_get_step(const lbm_domain* dom);
+lbm_status lbm_get_info(const lbm_domain* dom, lbm_geometry_info* info);
+int64_t lbm_get_tile_count(const lbm_domain* dom);
+
+/* Bytes of algorithmic HBM traffic of one step of this domain: 2 x 13
+ * populations per active cell at the storage precision plus one mask byte per
+ * tiled cell. */
+double lbm_step_bytes(const lbm_domain* dom);
+
+void lbm_destroy_domain(lbm_domain* dom);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,798 @@
+// C ABI of the solver (include/lbm.h): domain lifecycle, state
+// initialisation, stepping, the steady-state loop, observables and
+// read-back.  Compiled with -fmad=false: the FP64 initial state and read-back
+// follow the definitions operation for operation.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "kernel_body.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbm {
+bool build_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info* info,
+                std::string& err);
+void mark_near_boundary(uint8_t* m, int nx, int ny);
+
+cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
+                        int flip, int mode, Shape shape, int grid, cudaStream_t s) {
+    if (precision == 0) return launch_step_f64(insts, tiles, ntiles, flip, mode, shape, grid, s);
+    return launch_step_lp(precision, insts, tiles, ntiles, flip, mode, shape, grid, s);
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+// ---------------------------------------------------------------------------
+// errors
+static thread_local std::string g_err;
+
+static lbm_status fail(lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+extern "C" const char* lbm_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// memory layout of one domain inside the caller's buffer
+static constexpr size_t ALIGN = 256;
+static size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+static constexpr int MIN_TILE_AREA = 128;
+
+static size_t store_size(int prec) {
+    switch (prec) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16DEV: case LBM_BF16DEV: return 2;
+    default: return 0;
+    }
+}
+static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
+
+struct Layout {
+    int64_t npad, max_tiles;
+    size_t desc, obs, mask, tiles, partials, usnap, pops, total;
+};
+
+static int64_t max_tiles_for(int nx, int ny) {
+    int64_t best = 0;
+    for (int tw = 32; tw <= 256; tw *= 2) {
+        const int th = (MIN_TILE_AREA + tw - 1) / tw;
+        const int64_t n = (int64_t)((nx + tw - 1) / tw) * ((ny + th - 1) / th);
+        best = std::max(best, n);
+    }
+    return best;
+}
+
+static bool make_layout(int nx, int ny, int prec, Layout& L) {
+    const size_t ss = store_size(prec);
+    if (!ss || nx <= 0 || ny <= 0) return false;
+    const int64_t N = (int64_t)nx * ny;
+    L.npad = (N + 127) / 128 * 128;
+    L.max_tiles = max_tiles_for(nx, ny);
+    size_t off = 0;
+    L.desc = off; off = align_up(off + sizeof(InstDesc));
+    L.obs = off; off = align_up(off + NOBS * sizeof(double));
+    L.mask = off; off = align_up(off + (size_t)L.npad);
+    L.tiles = off; off = align_up(off + (size_t)L.max_tiles * sizeof(int4));
+    L.partials = off; off = align_up(off + (size_t)L.max_tiles * NPART * sizeof(double));
+    L.usnap = off; off = align_up(off + 2 * (size_t)L.npad * real_size(prec));
+    L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
+    L.total = off;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+struct lbm_domain {
+    int nx = 0, ny = 0, prec = 0;
+    int64_t N = 0;
+    Layout L{};
+    lbm_geometry_info info{};
+    std::vector<uint8_t> hmask;  // cell types with near-boundary bits
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    char* base = nullptr;
+    InstDesc h{};                // host copy of the device descriptor
+    InstDesc* d_desc = nullptr;
+    double* d_obs = nullptr;
+    int4* d_tiles = nullptr;
+    int ntiles = 0;
+    int64_t tiled_cells = 0;
+    lbm_launch launch{128, 1, 2, 0};
+    lbm_params params{};
+    bool have_params = false;
+    int64_t step = 0;
+    cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
+};
+
+// plain steps captured per CUDA graph (even, so a replay returns to the same parity)
+static constexpr int GRAPH_STEPS = 32;
+
+static bool launch_ok(const lbm_launch& l) {
+    const bool tw_ok = l.tile_w == 32 || l.tile_w == 64 || l.tile_w == 128 || l.tile_w == 256;
+    return tw_ok && l.block_rows >= 1 && l.rows_per_thread >= 1 && l.rows_per_thread <= 64 &&
+           l.tile_w * l.block_rows <= 256 &&
+           (int64_t)l.tile_w * l.block_rows * l.rows_per_thread >= MIN_TILE_AREA &&
+           l.blocks_per_sm >= 0 && l.blocks_per_sm <= 32;
+}
+
+static Shape shape_of(const lbm_launch& l) { return Shape{l.tile_w, l.block_rows, l.rows_per_thread}; }
+
+static int grid_of(const lbm_domain* d, int ntiles) {
+    if (d->launch.blocks_per_sm <= 0) return std::max(ntiles, 1);
+    return std::max(1, std::min(ntiles, d->launch.blocks_per_sm * d->num_sms));
+}
+
+// tile list: every tw x th tile holding at least one active cell
+static lbm_status build_tiles(lbm_domain* d) {
+    const int tw = d->launch.tile_w, th = d->launch.block_rows * d->launch.rows_per_thread;
+    std::vector<int4> tiles;
+    int64_t cells = 0;
+    for (int y0 = 0; y0 < d->ny; y0 += th) {
+        for (int x0 = 0; x0 < d->nx; x0 += tw) {
+            bool any = false;
+            for (int y = y0; y < std::min(d->ny, y0 + th) && !any; ++y)
+                for (int x = x0; x < std::min(d->nx, x0 + tw) && !any; ++x)
+                    any = (d->hmask[(int64_t)y * d->nx + x] & TYPE_BITS) <= POROUS;
+            if (any) {
+                tiles.push_back(make_int4(0, (int)tiles.size(), x0, y0));
+                cells += (int64_t)std::min(tw, d->nx - x0) * std::min(th, d->ny - y0);
+            }
+        }
+    }
+    if ((int64_t)tiles.size() > d->L.max_tiles) return fail(LBM_EINVAL, "tile list overflow");
+    d->ntiles = (int)tiles.size();
+    d->tiled_cells = cells;
+    d->h.ntiles = d->ntiles;
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(d->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, d->stream));
+    // pageable source: make sure the copy has consumed `tiles` before it dies
+    CK(cudaStreamSynchronize(d->stream));
+    return LBM_OK;
+}
+
+static lbm_status upload_desc(lbm_domain* d) {
+    CK(cudaMemcpyAsync(d->d_desc, &d->h, sizeof(InstDesc), cudaMemcpyHostToDevice, d->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels: initial state, read-back, write-back, finalisation
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t state) {
+    // SplitMix64 (Steele, Lea & Flood 2014)
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class ST>
+__global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, uint64_t seed) {
+    const InstDesc d = *dp;
+    using T = typename ST::T;
+    T* P = static_cast<T*>(d.pops);
+    const int64_t N = (int64_t)d.nx * d.ny;
+    // f^eq(p_out, u = 0), Eqs. 7-8: S_i(0) = w_i ((3*0 + 4.5*0*0) - 1.5*0)
+    double feq[9];
+    for (int i = 0; i < 9; ++i) {
+        const double Si = wgt(i) * (3.0 * 0.0 + 4.5 * 0.0 * 0.0 - 1.5 * 0.0);
+        const double a = i == 0 ? -4.0 * K_SIGMA : (i <= 4 ? K_LAMBDA : K_GAMMA);
+        feq[i] = a * d.p_out + Si;
+    }
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const bool act = (d.mask[c] & TYPE_BITS) <= POROUS;
+        if (!act) {
+            for (int q = 0; q < 13; ++q) P[q * d.npad + c] = T(0.0f);
+            continue;
+        }
+        double noise = 0.0;
+        if (noise_amp != 0.0) {
+            const uint64_t h = splitmix64(seed ^ (uint64_t)c);
+            const double u01 = (double)(h >> 11) * 0x1.0p-53;
+            noise = noise_amp * (2.0 * u01 - 1.0);
+        }
+        const double Ti = 0.25 * (d.T0 + noise);
+        for (int i = 0; i < 9; ++i) ST::stf(P + i * d.npad + c, (typename ST::R)feq[i], d);
+        for (int i = 1; i <= 4; ++i) ST::stT(P + (8 + i) * d.npad + c, (typename ST::R)Ti, d);
+    }
+}
+
+// natural-order population f_i (or T_i) of cell (x, y) at the given parity
+__device__ __forceinline__ int64_t slot_of(const InstDesc& d, int x, int y, int i, int parity,
+                                           bool heat) {
+    const int64_t c = (int64_t)y * d.nx + x;
+    if (parity == 0 || i == 0) return (heat ? (8 + i) : i) * d.npad + c;
+    // odd: f_i(x) sits in slot (x - e_i, opp(i))
+    int xs = x - ex(i), ys = y - ey(i);
+    if (xs < 0) xs += d.nx;
+    if (xs >= d.nx) xs -= d.nx;
+    if (ys < 0) ys += d.ny;
+    if (ys >= d.ny) ys -= d.ny;
+    const int o = opp(i);
+    return (heat ? (8 + o) : o) * d.npad + (int64_t)ys * d.nx + xs;
+}
+
+template <class ST>
+__global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, double* __restrict__ f,
+                                 double* __restrict__ g) {
+    const InstDesc d = *dp;
+    using T = typename ST::T;
+    const T* P = static_cast<const T*>(d.pops);
+    const int64_t N = (int64_t)d.nx * d.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const bool act = (d.mask[c] & TYPE_BITS) <= POROUS;
+        const int x = (int)(c % d.nx), y = (int)(c / d.nx);
+        for (int i = 0; i < 9; ++i)
+            if (f) f[i * N + c] = act ? (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d) : 0.0;
+        for (int i = 1; i <= 4; ++i)
+            if (g) g[(i - 1) * N + c] = act ? (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d) : 0.0;
+    }
+}
+
+template <class ST>
+__global__ void write_pops_kernel(const InstDesc* __restrict__ dp, int parity, const double* __restrict__ f,
+                                  const double* __restrict__ g) {
+    const InstDesc d = *dp;
+    using T = typename ST::T;
+    using R = typename ST::R;
+    T* P = static_cast<T*>(d.pops);
+    const int64_t N = (int64_t)d.nx * d.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if ((d.mask[c] & TYPE_BITS) > POROUS) continue;
+        const int x = (int)(c % d.nx), y = (int)(c / d.nx);
+        if (f)
+            for (int i = 0; i < 9; ++i) ST::stf(P + slot_of(d, x, y, i, parity, false), (R)f[i * N + c], d);
+        if (g)
+            for (int i = 1; i <= 4; ++i) ST::stT(P + slot_of(d, x, y, i, parity, true), (R)g[(i - 1) * N + c], d);
+    }
+}
+
+// Eq. 9 and Eq. 13 in FP64 on the stored populations
+template <class ST>
+__global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, double* __restrict__ u,
+                              double* __restrict__ p, double* __restrict__ Tf) {
+    const InstDesc d = *dp;
+    using T = typename ST::T;
+    const T* P = static_cast<const T*>(d.pops);
+    const int64_t N = (int64_t)d.nx * d.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const bool act = (d.mask[c] & TYPE_BITS) <= POROUS;
+        double ux = 0.0, uy = 0.0, pp = 0.0, TT = 0.0;
+        if (act) {
+            const int x = (int)(c % d.nx), y = (int)(c / d.nx);
+            double fv[9], gv[4];
+            for (int i = 0; i < 9; ++i) fv[i] = (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d);
+            for (int i = 1; i <= 4; ++i) gv[i - 1] = (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d);
+            ux = fv[1] - fv[3] + fv[5] - fv[6] - fv[7] + fv[8];
+            uy = fv[2] - fv[4] + fv[5] + fv[6] - fv[7] - fv[8];
+            const double usq = ux * ux + uy * uy;
+            const double S0 = K_W0 * (-1.5 * usq);
+            const double s = fv[1] + fv[2] + fv[3] + fv[4] + fv[5] + fv[6] + fv[7] + fv[8];
+            pp = (s + S0) / (4.0 * K_SIGMA);
+            TT = gv[0] + gv[1] + gv[2] + gv[3];
+        }
+        if (u) { u[c] = ux; u[N + c] = uy; }
+        if (p) p[c] = pp;
+        if (Tf) Tf[c] = TT;
+    }
+}
+
+// Folds the per-tile partials of each instance in a fixed order (one block per
+// instance, thread-strided then a fixed binary tree), so the result does not
+// depend on how tiles were scheduled or on which other instances ran.
+__global__ void __launch_bounds__(256) finalize_kernel(const InstDesc* __restrict__ insts) {
+    const InstDesc& d = insts[blockIdx.x];
+    __shared__ double sm[256][NPART];
+    double acc[NPART];
+    for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
+    const int nt = d.ntiles;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const double* q = d.partials + (int64_t)t * NPART;
+        for (int k = 0; k < NSUM; ++k) acc[k] += q[k];
+        for (int k = NSUM; k < NPART; ++k) acc[k] = fmax(acc[k], q[k]);
+    }
+    for (int k = 0; k < NPART; ++k) sm[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            for (int k = 0; k < NSUM; ++k) sm[threadIdx.x][k] += sm[threadIdx.x + s][k];
+            for (int k = NSUM; k < NPART; ++k)
+                sm[threadIdx.x][k] = fmax(sm[threadIdx.x][k], sm[threadIdx.x + s][k]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double* a = sm[0];
+        double* o = d.obs;
+        o[O_IOP] = a[P_N_FLUID] > 0.0 ? a[P_SUM_P] / a[P_N_FLUID] : 0.0;
+        o[O_Q_IN] = a[P_Q_IN];
+        o[O_Q_OUT] = a[P_Q_OUT];
+        o[O_MASS] = a[P_MASS];
+        o[O_PEAK] = a[P_PEAK];
+        o[O_WSS_C] = a[P_N_C] > 0.0 ? a[P_WSS_C] / a[P_N_C] : 0.0;
+        o[O_WSS_I] = a[P_N_I] > 0.0 ? a[P_WSS_I] / a[P_N_I] : 0.0;
+        o[O_RESID] = d.snap_valid ? a[P_RESID] : -1.0;
+        o[O_N_FLUID] = a[P_N_FLUID];
+        o[O_N_C] = a[P_N_C];
+        o[O_N_I] = a[P_N_I];
+        o[O_NAN] = (a[P_NAN] > 0.0 || !isfinite(a[P_SUM_P]) || !isfinite(a[P_MASS])) ? 1.0 : 0.0;
+    }
+}
+
+namespace lbm {
+cudaError_t launch_finalize(const InstDesc* insts, int ninst, cudaStream_t s) {
+    if (ninst <= 0) return cudaSuccess;
+    finalize_kernel<<<ninst, 256, 0, s>>>(insts);
+    return cudaGetLastError();
+}
+}  // namespace lbm
+
+static int ew_grid(const lbm_domain* d) {
+    const int64_t blocks = (d->N + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)d->num_sms * 16));
+}
+
+#define DISPATCH(prec, KERNEL, ...)                                                              \
+    switch (prec) {                                                                              \
+    case LBM_F64: KERNEL<StF64><<<ew_grid(d), 256, 0, d->stream>>>(__VA_ARGS__); break;          \
+    case LBM_F32: KERNEL<StF32><<<ew_grid(d), 256, 0, d->stream>>>(__VA_ARGS__); break;          \
+    case LBM_F16DEV: KERNEL<StF16><<<ew_grid(d), 256, 0, d->stream>>>(__VA_ARGS__); break;       \
+    default: KERNEL<StBF16><<<ew_grid(d), 256, 0, d->stream>>>(__VA_ARGS__); break;              \
+    }
+
+// ---------------------------------------------------------------------------
+// geometry (host only)
+
+extern "C" lbm_status lbm_build_mask(const lbm_geometry_desc* desc, uint8_t* host_out,
+                                     lbm_geometry_info* info) {
+    if (!desc) return fail(LBM_EINVAL, "null geometry");
+    std::string err;
+    if (!build_mask(*desc, host_out, info, err)) return fail(LBM_EINVAL, "%s", err.c_str());
+    return LBM_OK;
+}
+
+extern "C" size_t lbm_domain_bytes(const lbm_geometry_desc* desc, int32_t precision) {
+    if (!desc) return 0;
+    Layout L;
+    if (!make_layout(desc->nx, desc->ny, precision, L)) return 0;
+    return L.total;
+}
+
+extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t precision,
+                                        void* dev_buf, size_t bytes, void* stream,
+                                        lbm_domain** out) {
+    if (!desc || !out) return fail(LBM_EINVAL, "null argument");
+    *out = nullptr;
+    if (!store_size(precision)) return fail(LBM_EINVAL, "unknown precision %d", precision);
+    lbm_domain* d = new (std::nothrow) lbm_domain();
+    if (!d) return fail(LBM_ENOMEM, "host allocation failed");
+    d->nx = desc->nx;
+    d->ny = desc->ny;
+    d->prec = precision;
+    d->N = (int64_t)d->nx * d->ny;
+    std::string err;
+    if (d->nx <= 0 || d->ny <= 0 || !make_layout(d->nx, d->ny, precision, d->L)) {
+        delete d;
+        return fail(LBM_EINVAL, "invalid grid %d x %d", desc->nx, desc->ny);
+    }
+    d->hmask.assign((size_t)d->N, 0);
+    if (!build_mask(*desc, d->hmask.data(), &d->info, err)) {
+        delete d;
+        return fail(LBM_EINVAL, "%s", err.c_str());
+    }
+    mark_near_boundary(d->hmask.data(), d->nx, d->ny);
+    if (!dev_buf || bytes < d->L.total || (reinterpret_cast<uintptr_t>(dev_buf) % ALIGN) != 0) {
+        delete d;
+        return fail(LBM_ENOMEM, "device buffer too small or not 256-byte aligned (need %zu bytes)",
+                    d->L.total);
+    }
+    d->stream = static_cast<cudaStream_t>(stream);
+    d->base = static_cast<char*>(dev_buf);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete d;
+        return fail(LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    d->d_desc = reinterpret_cast<InstDesc*>(d->base + d->L.desc);
+    d->d_obs = reinterpret_cast<double*>(d->base + d->L.obs);
+    d->d_tiles = reinterpret_cast<int4*>(d->base + d->L.tiles);
+    InstDesc& h = d->h;
+    std::memset(&h, 0, sizeof(h));
+    h.pops = d->base + d->L.pops;
+    h.mask = reinterpret_cast<const uint8_t*>(d->base + d->L.mask);
+    h.usnap = d->base + d->L.usnap;
+    h.partials = reinterpret_cast<double*>(d->base + d->L.partials);
+    h.obs = d->d_obs;
+    h.npad = d->L.npad;
+    h.nx = d->nx;
+    h.ny = d->ny;
+    h.inlet_dir_x = d->info.inlet_dir_x;
+    h.inlet_dir_y = d->info.inlet_dir_y;
+    h.inlet_profile = d->info.inlet_profile;
+    h.inlet_lo = d->info.inlet_lo;
+    h.inlet_width = d->info.inlet_width > 0 ? d->info.inlet_width : 1;
+    h.eye_normals = d->info.eye_normals;
+    h.arc_xc = d->info.arc_xc;
+    h.arc_yc = d->info.arc_yc;
+    h.fscale = precision == LBM_F16DEV ? 4096.0 : 1.0;
+    h.finv = 1.0 / h.fscale;
+    lbm_status st;
+    cudaError_t ce = cudaMemcpyAsync(d->base + d->L.mask, d->hmask.data(), (size_t)d->N,
+                                     cudaMemcpyHostToDevice, d->stream);
+    if (ce != cudaSuccess) {
+        delete d;
+        return fail(LBM_ECUDA, "mask upload failed: %s", cudaGetErrorString(ce));
+    }
+    if ((st = build_tiles(d)) != LBM_OK || (st = upload_desc(d)) != LBM_OK) {
+        delete d;
+        return st;
+    }
+    *out = d;
+    return LBM_OK;
+}
+
+static void drop_graph(lbm_domain* d) {
+    if (d->graph) cudaGraphExecDestroy(d->graph);
+    d->graph = nullptr;
+}
+
+extern "C" void lbm_destroy_domain(lbm_domain* d) {
+    if (!d) return;
+    cudaStreamSynchronize(d->stream);
+    drop_graph(d);
+    delete d;
+}
+
+// ---------------------------------------------------------------------------
+// parameters
+
+static bool finite_all(const lbm_params& p) {
+    const double v[] = {p.tau, p.tau_T, p.g_beta, p.g_dir[0], p.g_dir[1], p.T_cold, p.T_hot,
+                        p.T0, p.T_in, p.u_in_max, p.K_tm, p.porosity, p.p_out, p.drive[0],
+                        p.drive[1], p.noise_amp, p.dx_m, p.dt_s, p.rho0, p.p_sc_pa};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// validates p and derives the descriptor's parameter fields (no upload)
+static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
+    if (!d || !p) return fail(LBM_EINVAL, "null argument");
+    if (!finite_all(*p)) return fail(LBM_EINVAL, "non-finite parameter");
+    if (!(p->tau > 0.5)) return fail(LBM_EINVAL, "tau must exceed 1/2 (nu > 0, Eq. 10)");
+    if (!(p->tau_T > 0.5)) return fail(LBM_EINVAL, "tau_T must exceed 1/2 (theta > 0, Eq. 14)");
+    if (!(p->K_tm > 0.0)) return fail(LBM_EINVAL, "K_tm must be positive");
+    const double gn = std::sqrt(p->g_dir[0] * p->g_dir[0] + p->g_dir[1] * p->g_dir[1]);
+    if (p->g_beta != 0.0 && std::fabs(gn - 1.0) > 1e-9) return fail(LBM_EINVAL, "g_dir must be a unit vector");
+    if (p->porosity < 0.0 || p->porosity > 1.0) return fail(LBM_EINVAL, "porosity must lie in [0, 1]");
+    if (p->rho0 < 0.0 || p->dx_m < 0.0 || p->dt_s < 0.0) return fail(LBM_EINVAL, "negative unit scale");
+    InstDesc& h = d->h;
+    h.omega = 1.0 / p->tau;
+    h.omegaT = 1.0 / p->tau_T;
+    h.g_beta = p->g_beta;
+    h.gx = p->g_dir[0];
+    h.gy = p->g_dir[1];
+    h.T_cold = p->T_cold;
+    h.T_hot = p->T_hot;
+    h.T0 = p->T0;
+    h.T_in = p->T_in;
+    h.u_in_max = p->u_in_max;
+    const double nu = (2.0 * p->tau - 1.0) / 6.0;  // Eq. 10
+    h.cK = nu / p->K_tm;
+    h.den = 1.0 + 0.5 * h.cK;
+    h.p_out = p->p_out;
+    h.drive_x = p->drive[0];
+    h.drive_y = p->drive[1];
+    h.kwss = -(1.0 - 1.0 / (2.0 * p->tau));
+    d->params = *p;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
+    lbm_status st = apply_params(d, p);
+    if (st != LBM_OK) return st;
+    const bool first = !d->have_params;
+    d->have_params = true;
+    if (first) return lbm_reset_state(d);
+    return upload_desc(d);
+}
+
+extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    if (!d->have_params) return fail(LBM_EINVAL, "set parameters before resetting the state");
+    const bool lowp = d->prec == LBM_F16DEV || d->prec == LBM_BF16DEV;
+    d->h.Tshift = lowp ? 0.25 * d->params.T0 : 0.0;
+    d->h.snap_valid = 0;
+    d->h.parity = 0;
+    lbm_status st = upload_desc(d);
+    if (st != LBM_OK) return st;
+    DISPATCH(d->prec, init_kernel, d->d_desc, d->params.noise_amp, d->params.seed);
+    CK(cudaGetLastError());
+    d->step = 0;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+
+static lbm_status step_once(lbm_domain* d, int mode) {
+    CK(launch_step(d->prec, d->d_desc, d->d_tiles, d->ntiles, (int)(d->step & 1), mode,
+                   shape_of(d->launch), grid_of(d, d->ntiles), d->stream));
+    if (mode == 0 || (mode & OBS_WRITE)) d->step += 1;
+    return LBM_OK;
+}
+
+static const void* step_fn(int prec, bool obs) {
+    return prec == LBM_F64 ? step_kernel_ptr_f64(obs) : step_kernel_ptr_lp(prec, obs);
+}
+
+// Builds (once per launch shape) a graph of GRAPH_STEPS chained plain steps
+// with alternating parity, replayed by lbm_step from an even step.
+static lbm_status ensure_graph(lbm_domain* d) {
+    if (d->graph) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    const Shape sh = shape_of(d->launch);
+    const int grid = grid_of(d, d->ntiles);
+    cudaGraphNode_t prev = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k) {
+        const InstDesc* a0 = d->d_desc;
+        const int4* a1 = d->d_tiles;
+        int a2 = d->ntiles, a3 = k & 1, a4 = 0;
+        Shape a5 = sh;
+        void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(step_fn(d->prec, false));
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(sh.tw, sh.bh);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&d->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        d->graph = nullptr;
+        return fail(LBM_ECUDA, "graph construction failed: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_domain* d, int64_t nsteps) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    int64_t k = 0;
+    lbm_status st;
+    if (nsteps >= GRAPH_STEPS + 1 && d->ntiles > 0) {
+        if (d->step & 1) {
+            if ((st = step_once(d, 0)) != LBM_OK) return st;
+            ++k;
+        }
+        if ((st = ensure_graph(d)) != LBM_OK) return st;
+        while (nsteps - k >= GRAPH_STEPS) {
+            CK(cudaGraphLaunch(d->graph, d->stream));
+            d->step += GRAPH_STEPS;
+            k += GRAPH_STEPS;
+        }
+    }
+    for (; k < nsteps; ++k)
+        if ((st = step_once(d, 0)) != LBM_OK) return st;
+    return LBM_OK;
+}
+
+static lbm_status fetch_obs(lbm_domain* d, double* o) {
+    CK(launch_finalize(d->d_desc, 1, d->stream));
+    CK(cudaMemcpyAsync(o, d->d_obs, NOBS * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return LBM_OK;
+}
+
+static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out) {
+    const lbm_params& p = d->params;
+    const double scale = p.dt_s > 0.0 ? p.rho0 * (p.dx_m / p.dt_s) * (p.dx_m / p.dt_s) : 0.0;
+    std::memset(out, 0, sizeof(*out));
+    out->step = step;
+    out->iop = o[O_IOP];
+    out->iop_pa = p.p_sc_pa + scale * (o[O_IOP] - p.p_out);
+    out->q_in = o[O_Q_IN];
+    out->q_out = o[O_Q_OUT];
+    out->mass = o[O_MASS];
+    out->peak_speed = o[O_PEAK];
+    out->wss_cornea = o[O_WSS_C];
+    out->wss_iris = o[O_WSS_I];
+    out->wss_cornea_pa = scale * o[O_WSS_C];
+    out->wss_iris_pa = scale * o[O_WSS_I];
+    out->residual = o[O_RESID];
+    out->n_fluid = (int64_t)o[O_N_FLUID];
+    out->n_cornea = (int64_t)o[O_N_C];
+    out->n_iris = (int64_t)o[O_N_I];
+    out->nan_flag = o[O_NAN] != 0.0;
+}
+
+extern "C" lbm_status lbm_read_observables(lbm_domain* d, lbm_observables* out) {
+    if (!d || !out) return fail(LBM_EINVAL, "null argument");
+    if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
+    const int mode = OBS_STATS | (d->h.snap_valid ? OBS_RESID : 0);
+    lbm_status st = step_once(d, mode);
+    if (st != LBM_OK) return st;
+    double o[NOBS];
+    if ((st = fetch_obs(d, o)) != LBM_OK) return st;
+    fill_obs(d, o, d->step, out);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check_every,
+                                        int64_t max_steps, int64_t* steps_out) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
+    if (check_every < 1 || max_steps < 0 || !(tol >= 0.0)) return fail(LBM_EINVAL, "bad steady-state arguments");
+    int64_t taken = 0;
+    lbm_status st = LBM_OK;
+    double o[NOBS];
+    if (steps_out) *steps_out = 0;
+    while (taken < max_steps) {
+        if ((st = lbm_step(d, check_every - 1)) != LBM_OK) return st;
+        const bool had_snap = d->h.snap_valid != 0;
+        if ((st = step_once(d, OBS_STATS | OBS_SNAP | OBS_WRITE | (had_snap ? OBS_RESID : 0))) != LBM_OK)
+            return st;
+        if ((st = fetch_obs(d, o)) != LBM_OK) return st;
+        taken += check_every;
+        if (steps_out) *steps_out = taken;
+        if (o[O_NAN] != 0.0) return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
+        if (!had_snap) {
+            d->h.snap_valid = 1;
+            if ((st = upload_desc(d)) != LBM_OK) return st;
+        } else if (o[O_RESID] < tol) {
+            return LBM_OK;
+        }
+    }
+    return fail(LBM_ENOTCONVERGED, "not steady after %lld steps", (long long)taken);
+}
+
+// ---------------------------------------------------------------------------
+// read-back, write-back, checkpoints
+
+extern "C" lbm_status lbm_read_field(lbm_domain* d, double* u, double* p, double* T) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    DISPATCH(d->prec, fields_kernel, d->d_desc, (int)(d->step & 1), u, p, T);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_populations(lbm_domain* d, double* f, double* g) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    DISPATCH(d->prec, read_pops_kernel, d->d_desc, (int)(d->step & 1), f, g);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_write_populations(lbm_domain* d, const double* f, const double* g) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
+    DISPATCH(d->prec, write_pops_kernel, d->d_desc, (int)(d->step & 1), f, g);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, prec, snap_valid;
+    int64_t step, npad;
+    double Tshift;
+    lbm_params params;
+};
+}  // namespace
+
+extern "C" size_t lbm_state_bytes(const lbm_domain* d) {
+    if (!d) return 0;
+    return sizeof(StateHeader) + 13 * (size_t)d->L.npad * store_size(d->prec);
+}
+
+extern "C" lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes) {
+    if (!d || !host_buf) return fail(LBM_EINVAL, "null argument");
+    if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
+    if (bytes < lbm_state_bytes(d)) return fail(LBM_ENOMEM, "state buffer too small");
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LBMSTAT1", 8);
+    hd.nx = d->nx;
+    hd.ny = d->ny;
+    hd.prec = d->prec;
+    hd.snap_valid = 0;
+    hd.step = d->step;
+    hd.npad = d->L.npad;
+    hd.Tshift = d->h.Tshift;
+    hd.params = d->params;
+    std::memcpy(host_buf, &hd, sizeof(hd));
+    CK(cudaMemcpyAsync(static_cast<char*>(host_buf) + sizeof(hd), d->h.pops,
+                       13 * (size_t)d->L.npad * store_size(d->prec), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t bytes) {
+    if (!d || !host_buf) return fail(LBM_EINVAL, "null argument");
+    if (bytes < lbm_state_bytes(d)) return fail(LBM_ENOMEM, "state buffer too small");
+    StateHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "LBMSTAT1", 8) != 0 || hd.nx != d->nx || hd.ny != d->ny ||
+        hd.prec != d->prec || hd.npad != d->L.npad)
+        return fail(LBM_EINVAL, "checkpoint does not match this domain");
+    lbm_status st = apply_params(d, &hd.params);  // no reset: populations come from the buffer
+    if (st != LBM_OK) return st;
+    d->have_params = true;
+    d->h.Tshift = hd.Tshift;
+    d->h.snap_valid = 0;
+    d->step = hd.step;
+    if ((st = upload_desc(d)) != LBM_OK) return st;
+    CK(cudaMemcpyAsync(d->h.pops, static_cast<const char*>(host_buf) + sizeof(hd),
+                       13 * (size_t)d->L.npad * store_size(d->prec), cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shape and introspection
+
+extern "C" lbm_status lbm_set_launch(lbm_domain* d, const lbm_launch* l) {
+    if (!d || !l) return fail(LBM_EINVAL, "null argument");
+    if (!launch_ok(*l)) return fail(LBM_EINVAL, "invalid launch shape");
+    CK(cudaStreamSynchronize(d->stream));
+    drop_graph(d);
+    d->launch = *l;
+    lbm_status st = build_tiles(d);
+    if (st != LBM_OK) return st;
+    return upload_desc(d);
+}
+
+extern "C" lbm_status lbm_get_launch(const lbm_domain* d, lbm_launch* l) {
+    if (!d || !l) return fail(LBM_EINVAL, "null argument");
+    *l = d->launch;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_get_step(const lbm_domain* d) { return d ? d->step : -1; }
+
+extern "C" lbm_status lbm_get_info(const lbm_domain* d, lbm_geometry_info* info) {
+    if (!d || !info) return fail(LBM_EINVAL, "null argument");
+    *info = d->info;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_get_tile_count(const lbm_domain* d) { return d ? d->ntiles : -1; }
+
+extern "C" double lbm_step_bytes(const lbm_domain* d) {
+    if (!d) return 0.0;
+    return (double)d->info.n_active * (26.0 * (double)store_size(d->prec) + 1.0);
+}

@@ -1,0 +1,139 @@
+// Internal declarations shared by the library's translation units: the
+// per-instance descriptor read by the kernels, the mask encoding, the
+// storage-precision traits and the launcher entry points.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Mask byte: bits 0-2 cell type (lbm_cell_type), bit 3 set when at least one
+// of the eight neighbours is not an active (fluid or porous) cell.
+constexpr uint8_t TYPE_BITS = 7;
+constexpr uint8_t NEAR_BOUNDARY = 8;
+enum : int { FLUID = 0, POROUS = 1, COLD = 2, HOT = 3, ADIABATIC = 4, INLET = 5, OUTLET = 6 };
+
+// Observation modes of the fused step (bit set).
+enum : int {
+    OBS_STATS = 1,  // per-tile partial sums of the observables
+    OBS_RESID = 2,  // max |u - u_snapshot|
+    OBS_SNAP = 4,   // store u as the new snapshot
+    OBS_WRITE = 8   // also perform the step (else observe only)
+};
+
+// Per-tile partial slots (FP64).
+enum : int {
+    P_SUM_P = 0, P_N_FLUID, P_MASS, P_Q_IN, P_Q_OUT, P_WSS_C, P_N_C, P_WSS_I, P_N_I,
+    P_NAN, P_PEAK, P_RESID, NPART
+};
+constexpr int NSUM = P_PEAK;  // slots [0, NSUM) add, the rest take the max
+
+// Finalised observables (FP64) as written by the finalize kernel.
+enum : int {
+    O_IOP = 0, O_Q_IN, O_Q_OUT, O_MASS, O_PEAK, O_WSS_C, O_WSS_I, O_RESID,
+    O_N_FLUID, O_N_C, O_N_I, O_NAN, NOBS
+};
+
+// Everything a kernel needs to update one problem instance.  Lives in device
+// memory (one per domain, one table per batch); copied to shared memory by
+// every block that works on the instance.
+struct InstDesc {
+    void* pops;          // 13 planes of npad elements: f_0..f_8, T_1..T_4
+    const uint8_t* mask; // npad bytes
+    void* usnap;         // 2 planes of npad compute-precision values
+    double* partials;    // NPART doubles per tile of this instance
+    double* obs;         // NOBS finalised observables
+    int64_t npad;
+    int32_t ntiles;      // tiles of this instance (partials rows)
+    int32_t pad0;
+    int32_t nx, ny;
+    int32_t parity;      // parity of the instance's step counter at launch base
+    int32_t snap_valid;
+    int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
+    int32_t eye_normals;
+    double arc_xc, arc_yc;
+    // parameters, lattice units, derived on the host
+    double omega, omegaT;       // 1/tau, 1/tau_T
+    double g_beta, gx, gy;
+    double T_cold, T_hot, T0, T_in;
+    double u_in_max;
+    double cK, den;             // nu/K and 1 + nu/(2K)
+    double p_out;
+    double drive_x, drive_y;
+    double kwss;                // -(1 - 1/(2 tau))
+    // 16-bit storage: stored = (value - shift) * scale
+    double fscale, finv, Tshift;
+};
+static_assert(sizeof(InstDesc) % 8 == 0, "descriptor must be 8-byte sized");
+
+struct Shape {
+    int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = tw x bh threads
+};
+
+// ---- storage traits --------------------------------------------------------
+struct StF64 {
+    using T = double;
+    using R = double;
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return *p; }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { *p = v; }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
+};
+struct StF32 {
+    using T = float;
+    using R = float;
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return *p; }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { *p = v; }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
+};
+struct StF16 {
+    using T = __half;
+    using R = float;
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
+        return __half2float(*p) * (float)d.finv;
+    }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
+        *p = __float2half_rn(v * (float)d.fscale);
+    }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
+        return __half2float(*p) * (float)d.finv + (float)d.Tshift;
+    }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
+        *p = __float2half_rn((v - (float)d.Tshift) * (float)d.fscale);
+    }
+};
+struct StBF16 {
+    using T = __nv_bfloat16;
+    using R = float;
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
+        return __bfloat162float(*p) * (float)d.finv;
+    }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
+        *p = __float2bfloat16_rn(v * (float)d.fscale);
+    }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
+        return __bfloat162float(*p) * (float)d.finv + (float)d.Tshift;
+    }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
+        *p = __float2bfloat16_rn((v - (float)d.Tshift) * (float)d.fscale);
+    }
+};
+
+// ---- launchers (one translation unit per arithmetic precision) -----------
+// precision: 0 f64, 1 f32, 2 f16-dev, 3 bf16-dev.
+cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
+                        int flip, int mode, Shape shape, int grid, cudaStream_t s);
+cudaError_t launch_step_f64(const InstDesc* insts, const int4* tiles, int ntiles, int flip,
+                            int mode, Shape shape, int grid, cudaStream_t s);
+cudaError_t launch_step_lp(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
+                           int flip, int mode, Shape shape, int grid, cudaStream_t s);
+cudaError_t launch_finalize(const InstDesc* insts, int ninst, cudaStream_t s);
+// device entry of the step kernel (for CUDA graph kernel nodes)
+const void* step_kernel_ptr_f64(bool obs);
+const void* step_kernel_ptr_lp(int precision, bool obs);
+
+}  // namespace lbm
