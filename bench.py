@@ -300,7 +300,7 @@ def run_gpu(args):
     return 0
 
 
-LAUNCH = dict(tile_w=128, block_rows=1, rows_per_thread=2, blocks_per_sm=0)
+LAUNCH = dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0)
 
 
 def main():

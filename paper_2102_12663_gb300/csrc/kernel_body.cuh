@@ -111,7 +111,8 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     nb[8] = yd + xr;
 
     T* const P = static_cast<T*>(d.pops);
-    const int64_t np = d.npad;
+    const int np = (int)d.npad;  // 13 * npad < 2^31 (checked at creation)
+    const Phys<R>& ph = phys<R>(d);
 
     // ---- load (AA read pattern) -------------------------------------------
     // The mask and all 13 populations are requested together (every slot
@@ -203,7 +204,8 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
                         const double pxx = d1 + d3 + d5 + d6 + d7 + d8;
                         const double pxy = d5 - d6 + d7 - d8;
                         const double pyy = d2 + d4 + d5 + d6 + d7 + d8;
-                        const double sxx = d.kwss * pxx, sxy = d.kwss * pxy, syy = d.kwss * pyy;
+                        const double kw = d.pd.kwss;
+                        const double sxx = kw * pxx, sxy = kw * pxy, syy = kw * pyy;
                         if (hit_c) {
                             double ax = ac_x, ay = ac_y;
                             if (d.eye_normals) { ax = x - d.arc_xc; ay = y - d.arc_yc; }
@@ -239,13 +241,13 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     }
 
     // ---- body force, Eqs. 15-17: F_i = (1/2) e_i . F on the axis links --------
-    const R gb = R(d.g_beta) * (Tm - R(d.T0));
-    const R Fx = R(d.drive_x) - gb * R(d.gx);
-    const R Fy = R(d.drive_y) - gb * R(d.gy);
+    const R gb = ph.g_beta * (Tm - ph.T0);
+    const R Fx = ph.drive_x - gb * ph.gx;
+    const R Fy = ph.drive_y - gb * ph.gy;
     const R F1 = R(0.5) * Fx, F2 = R(0.5) * Fy;
 
     // ---- flow collision, Eq. 6 --------------------------------------------
-    const R om = R(d.omega);
+    const R om = ph.omega;
     R fs[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fs[i] = f[i] - om * (f[i] - feq[i]);
@@ -256,7 +258,7 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
 
     // ---- Darcy drag in porous cells, Eq. 4 at the mid-step velocity ---------
     if (type == POROUS) {
-        const R den = R(d.den), cK = R(d.cK);
+        const R den = ph.den, cK = ph.cK;
         const R umx = (ux + R(0.5) * Fx) / den;
         const R umy = (uy + R(0.5) * Fy) / den;
         const R FDx = -cK * umx;
@@ -273,7 +275,7 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     }
 
     // ---- heat collision, Eqs. 11-12 ----------------------------------------
-    const R omT = R(d.omegaT);
+    const R omT = ph.omegaT;
     const R Tq = R(0.25) * Tm;
     R gs[4];
 #pragma unroll
@@ -304,14 +306,14 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
                     const R s = (R(cg - d.inlet_lo) + R(0.5)) / R(d.inlet_width);
                     shape = R(4.0) * s * (R(1.0) - s);
                 }
-                const R uin = R(d.u_in_max) * shape;
+                const R uin = ph.u_in_max * shape;
                 const R uix = uin * R(d.inlet_dir_x), uiy = uin * R(d.inlet_dir_y);
                 v = fs[i] - R(6.0 * wgt(i)) * (R(ex(i)) * uix + R(ey(i)) * uiy);
                 if (OBS) q_in += (double)(v - fs[i]);
             } else if (tn == OUTLET) {
                 // pressure anti-bounce-back: minus f* plus the even part of feq(p_out, u)
                 const R kap = i <= 4 ? R(K_LAMBDA) : R(K_GAMMA);
-                v = -fs[i] + R(2.0) * (kap * R(d.p_out) +
+                v = -fs[i] + R(2.0) * (kap * ph.p_out +
                                        R(wgt(i)) * (R(4.5) * eu[i] * eu[i] - R(1.5) * usq));
                 if (OBS) q_out += (double)(fs[i] - v);
             }
@@ -329,9 +331,9 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
         R v = gs[i - 1];
         if (is_bnd) {
             const uint32_t tn = (ntypes >> (4 * (i - 1))) & 15u;
-            if (tn == COLD) v = -gs[i - 1] + R(0.5) * R(d.T_cold);
-            else if (tn == HOT) v = -gs[i - 1] + R(0.5) * R(d.T_hot);
-            else if (tn == INLET) v = -gs[i - 1] + R(0.5) * R(d.T_in);
+            if (tn == COLD) v = -gs[i - 1] + R(0.5) * ph.T_cold;
+            else if (tn == HOT) v = -gs[i - 1] + R(0.5) * ph.T_hot;
+            else if (tn == INLET) v = -gs[i - 1] + R(0.5) * ph.T_in;
             else if (tn == OUTLET) v = -gs[i - 1] + R(0.5) * Tm;
             // adiabatic: bounce-back, zero heat flux
         }
@@ -348,7 +350,7 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
 }
 
 template <class ST, bool OBS>
-__global__ void __launch_bounds__(256, (OBS || sizeof(typename ST::R) == 8) ? 2 : 4) step_kernel(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(256, (OBS || sizeof(typename ST::R) == 8) ? 2 : (sizeof(typename ST::T) == 2 ? 3 : 4)) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
     __shared__ __align__(16) InstDesc sd;

@@ -88,6 +88,7 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     if (!ss || nx <= 0 || ny <= 0) return false;
     const int64_t N = (int64_t)nx * ny;
     L.npad = (N + 127) / 128 * 128;
+    if (13 * L.npad > (int64_t)INT32_MAX) return false;  // kernels index planes in 32 bits
     L.max_tiles = max_tiles_for(nx, ny);
     size_t off = 0;
     L.desc = off; off = align_up(off + sizeof(InstDesc));
@@ -198,7 +199,7 @@ __global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, u
     for (int i = 0; i < 9; ++i) {
         const double Si = wgt(i) * (3.0 * 0.0 + 4.5 * 0.0 * 0.0 - 1.5 * 0.0);
         const double a = i == 0 ? -4.0 * K_SIGMA : (i <= 4 ? K_LAMBDA : K_GAMMA);
-        feq[i] = a * d.p_out + Si;
+        feq[i] = a * d.pd.p_out + Si;
     }
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -213,7 +214,7 @@ __global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, u
             const double u01 = (double)(h >> 11) * 0x1.0p-53;
             noise = noise_amp * (2.0 * u01 - 1.0);
         }
-        const double Ti = 0.25 * (d.T0 + noise);
+        const double Ti = 0.25 * (d.pd.T0 + noise);
         for (int i = 0; i < 9; ++i) ST::stf(P + i * d.npad + c, (typename ST::R)feq[i], d);
         for (int i = 1; i <= 4; ++i) ST::stT(P + (8 + i) * d.npad + c, (typename ST::R)Ti, d);
     }
@@ -441,8 +442,8 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     h.eye_normals = d->info.eye_normals;
     h.arc_xc = d->info.arc_xc;
     h.arc_yc = d->info.arc_yc;
-    h.fscale = precision == LBM_F16DEV ? 4096.0 : 1.0;
-    h.finv = 1.0 / h.fscale;
+    h.fscale = precision == LBM_F16DEV ? 4096.0f : 1.0f;
+    h.finv = 1.0f / h.fscale;
     lbm_status st;
     cudaError_t ce = cudaMemcpyAsync(d->base + d->L.mask, d->hmask.data(), (size_t)d->N,
                                      cudaMemcpyHostToDevice, d->stream);
@@ -493,7 +494,7 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     if (p->g_beta != 0.0 && std::fabs(gn - 1.0) > 1e-9) return fail(LBM_EINVAL, "g_dir must be a unit vector");
     if (p->porosity < 0.0 || p->porosity > 1.0) return fail(LBM_EINVAL, "porosity must lie in [0, 1]");
     if (p->rho0 < 0.0 || p->dx_m < 0.0 || p->dt_s < 0.0) return fail(LBM_EINVAL, "negative unit scale");
-    InstDesc& h = d->h;
+    Phys<double>& h = d->h.pd;
     h.omega = 1.0 / p->tau;
     h.omegaT = 1.0 / p->tau_T;
     h.g_beta = p->g_beta;
@@ -511,6 +512,23 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     h.drive_x = p->drive[0];
     h.drive_y = p->drive[1];
     h.kwss = -(1.0 - 1.0 / (2.0 * p->tau));
+    Phys<float>& f = d->h.pf;
+    f.omega = (float)h.omega;
+    f.omegaT = (float)h.omegaT;
+    f.g_beta = (float)h.g_beta;
+    f.gx = (float)h.gx;
+    f.gy = (float)h.gy;
+    f.T_cold = (float)h.T_cold;
+    f.T_hot = (float)h.T_hot;
+    f.T0 = (float)h.T0;
+    f.T_in = (float)h.T_in;
+    f.u_in_max = (float)h.u_in_max;
+    f.cK = (float)h.cK;
+    f.den = (float)h.den;
+    f.p_out = (float)h.p_out;
+    f.drive_x = (float)h.drive_x;
+    f.drive_y = (float)h.drive_y;
+    f.kwss = (float)h.kwss;
     d->params = *p;
     return LBM_OK;
 }
@@ -528,7 +546,7 @@ extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
     if (!d) return fail(LBM_EINVAL, "null domain");
     if (!d->have_params) return fail(LBM_EINVAL, "set parameters before resetting the state");
     const bool lowp = d->prec == LBM_F16DEV || d->prec == LBM_BF16DEV;
-    d->h.Tshift = lowp ? 0.25 * d->params.T0 : 0.0;
+    d->h.Tshift = lowp ? (float)(0.25 * d->params.T0) : 0.0f;
     d->h.snap_valid = 0;
     d->h.parity = 0;
     lbm_status st = upload_desc(d);

@@ -37,6 +37,20 @@ enum : int {
     O_N_FLUID, O_N_C, O_N_I, O_NAN, NOBS
 };
 
+// Physical parameters in the arithmetic precision of a kernel (derived once on
+// the host, so no kernel converts between FP64 and FP32 per cell).
+template <class R>
+struct Phys {
+    R omega, omegaT;      // 1/tau, 1/tau_T
+    R g_beta, gx, gy;
+    R T_cold, T_hot, T0, T_in;
+    R u_in_max;
+    R cK, den;            // nu/K and 1 + nu/(2K)
+    R p_out;
+    R drive_x, drive_y;
+    R kwss;               // -(1 - 1/(2 tau))
+};
+
 // Everything a kernel needs to update one problem instance.  Lives in device
 // memory (one per domain, one table per batch); copied to shared memory by
 // every block that works on the instance.
@@ -48,26 +62,26 @@ struct InstDesc {
     double* obs;         // NOBS finalised observables
     int64_t npad;
     int32_t ntiles;      // tiles of this instance (partials rows)
-    int32_t pad0;
     int32_t nx, ny;
     int32_t parity;      // parity of the instance's step counter at launch base
     int32_t snap_valid;
     int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
     int32_t eye_normals;
+    int32_t pad0;
     double arc_xc, arc_yc;
-    // parameters, lattice units, derived on the host
-    double omega, omegaT;       // 1/tau, 1/tau_T
-    double g_beta, gx, gy;
-    double T_cold, T_hot, T0, T_in;
-    double u_in_max;
-    double cK, den;             // nu/K and 1 + nu/(2K)
-    double p_out;
-    double drive_x, drive_y;
-    double kwss;                // -(1 - 1/(2 tau))
+    Phys<double> pd;
+    Phys<float> pf;
     // 16-bit storage: stored = (value - shift) * scale
-    double fscale, finv, Tshift;
+    float fscale, finv, Tshift, pad1;
 };
 static_assert(sizeof(InstDesc) % 8 == 0, "descriptor must be 8-byte sized");
+
+template <class R>
+__host__ __device__ __forceinline__ const Phys<R>& phys(const InstDesc& d);
+template <>
+__host__ __device__ __forceinline__ const Phys<double>& phys<double>(const InstDesc& d) { return d.pd; }
+template <>
+__host__ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDesc& d) { return d.pf; }
 
 struct Shape {
     int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = tw x bh threads
@@ -94,32 +108,32 @@ struct StF16 {
     using T = __half;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
-        return __half2float(*p) * (float)d.finv;
+        return __half2float(*p) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        *p = __float2half_rn(v * (float)d.fscale);
+        *p = __float2half_rn(v * d.fscale);
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __half2float(*p) * (float)d.finv + (float)d.Tshift;
+        return __half2float(*p) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        *p = __float2half_rn((v - (float)d.Tshift) * (float)d.fscale);
+        *p = __float2half_rn((v - d.Tshift) * d.fscale);
     }
 };
 struct StBF16 {
     using T = __nv_bfloat16;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
-        return __bfloat162float(*p) * (float)d.finv;
+        return __bfloat162float(*p) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        *p = __float2bfloat16_rn(v * (float)d.fscale);
+        *p = __float2bfloat16_rn(v * d.fscale);
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __bfloat162float(*p) * (float)d.finv + (float)d.Tshift;
+        return __bfloat162float(*p) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        *p = __float2bfloat16_rn((v - (float)d.Tshift) * (float)d.fscale);
+        *p = __float2bfloat16_rn((v - d.Tshift) * d.fscale);
     }
 };
 
