@@ -253,6 +253,25 @@ double lbm_step_bytes(const lbm_domain* dom);
 
 void lbm_destroy_domain(lbm_domain* dom);
 
+/* ---- observables without caller-provided reduction scratch ----------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * may not allocate device memory once they are running, for instance a host
+ * application that hands the library a fixed device budget at start-up, or a
+ * latency-critical loop in which an allocation would stall the device.  It
+ * returns the same observables as lbm_read_observables (FP64 sums, folded in
+ * a different fixed order), but keeps its per-row partial sums in a device
+ * array inside the library instead of the domain buffer: LBM_NOALLOC_MAX_ROWS
+ * rows x 12 doubles (about 0.8 MB), held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address with the device current; make that first call before any
+ * stream capture.  A grid with more than LBM_NOALLOC_MAX_ROWS rows is
+ * rejected with LBM_EINVAL.  All calls on one device share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU (for example
+ * on two streams with no ordering between them) race on it, calls on one
+ * stream do not.  Synchronises the domain's stream. */
+#define LBM_NOALLOC_MAX_ROWS 8192
+lbm_status lbm_read_observables_noalloc(lbm_domain* dom, lbm_observables* out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

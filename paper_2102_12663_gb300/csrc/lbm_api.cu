@@ -814,3 +814,26 @@ extern "C" double lbm_step_bytes(const lbm_domain* d) {
     if (!d) return 0.0;
     return (double)d->info.n_active * (26.0 * (double)store_size(d->prec) + 1.0);
 }
+
+// ---------------------------------------------------------------------------
+// internal accessors for the allocation-free observables entry point
+namespace lbm {
+lbm_status set_error(lbm_status s, const char* msg) { return fail(s, "%s", msg); }
+
+bool domain_parts(const lbm_domain* d, const InstDesc** desc, int* precision, int* ny,
+                  int* parity, int* snap_valid, cudaStream_t* stream) {
+    if (!d) { fail(LBM_EINVAL, "null domain"); return false; }
+    if (!d->have_params) { fail(LBM_EINVAL, "parameters not set"); return false; }
+    *desc = d->d_desc;
+    *precision = d->prec;
+    *ny = d->ny;
+    *parity = (int)(d->step & 1);
+    *snap_valid = d->h.snap_valid;
+    *stream = d->stream;
+    return true;
+}
+
+void fill_observables(const lbm_domain* d, const double* o, lbm_observables* out) {
+    fill_obs(d, o, d->step, out);
+}
+}  // namespace lbm

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "lbm_step": (i32, [dom, i64]),
         "lbm_run_to_steady": (i32, [dom, dbl, i32, i64, P(i64)]),
         "lbm_read_observables": (i32, [dom, P(Observables)]),
+        "lbm_read_observables_noalloc": (i32, [dom, P(Observables)]),
         "lbm_read_field": (i32, [dom, vp, vp, vp]),
         "lbm_read_populations": (i32, [dom, vp, vp]),
         "lbm_write_populations": (i32, [dom, vp, vp]),
@@ -286,6 +287,12 @@ class Domain:
     def observables(self) -> dict:
         o = Observables()
         check(self._L.lbm_read_observables(self._h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Observables._fields_}
+
+    def observables_noalloc(self) -> dict:
+        """Same as observables(), with the library's own reduction scratch."""
+        o = Observables()
+        check(self._L.lbm_read_observables_noalloc(self._h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in Observables._fields_}
 
     def fields(self):
