@@ -310,10 +310,35 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling driver: run this many single fused steps of the "
+                         "workload (no timing, no JSON line) and exit")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16", "f64"],
+                    help="storage precision for --profile")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_gpu(args)
+
+
+def run_profile(args):
+    """A short, fixed sequence of single-step launches for ncu captures."""
+    import torch
+
+    from paper_2102_12663_gb300 import lbm
+    lbm.load(build_if_missing=True)
+    dom = lbm.Domain(dict(nx=NX, ny=NY, angle_deg=45.0), precision=args.precision)
+    dom.set_launch(**LAUNCH)
+    dom.set_params(eye_params())
+    for _ in range(args.profile):
+        dom.step(1)
+    torch.cuda.synchronize()
+    print(f"profile driver: {args.profile} steps, {dom.tile_count()} tiles, "
+          f"{dom.step_bytes():.0f} algorithmic bytes per step", flush=True)
+    dom.close()
+    return 0
 
 
 if __name__ == "__main__":
