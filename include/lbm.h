@@ -253,6 +253,68 @@ double lbm_step_bytes(const lbm_domain* dom);
 
 void lbm_destroy_domain(lbm_domain* dom);
 
+/* ---- batches: many problems, one launch per time step --------------------
+ * A batch advances many domains of one storage precision, of any sizes and
+ * parameters, with a single launch of the fused step per time step over the
+ * concatenated tile lists of its members (and, for 32 or more steps, replays
+ * of a CUDA graph of those launches).  Each member keeps its own state,
+ * parameters and step counter; a member's results do not depend on which
+ * other domains share the batch: populations are bit-identical to stepping it
+ * alone with the same launch shape, and its observables are folded from its
+ * own tiles in a fixed order.  While a domain belongs to a batch its work
+ * runs on the batch's stream.  Device memory of the batch (member table,
+ * tile list, observables) belongs to the caller: lbm_batch_bytes. */
+
+/* Bytes for a batch of up to max_instances members holding max_tiles tiles
+ * in total (sum of lbm_get_tile_count of the members at the batch's shape). */
+size_t lbm_batch_bytes(int32_t max_instances, int64_t max_tiles);
+
+/* Create an empty batch.  launch (may be NULL) is the shape every member is
+ * switched to when it joins. */
+lbm_status lbm_batch_create(int32_t precision, int32_t max_instances, int64_t max_tiles,
+                            const lbm_launch* launch, void* dev_buf, size_t bytes,
+                            void* stream, lbm_batch** out);
+
+/* Add a domain (same precision, parameters set) / remove it.  EBUSY when the
+ * batch is full or its tile capacity would be exceeded.  Adding synchronises
+ * the domain's own stream; removing synchronises the batch's stream and gives
+ * the domain its own stream back. */
+lbm_status lbm_batch_add(lbm_batch* b, lbm_domain* dom);
+lbm_status lbm_batch_remove(lbm_batch* b, lbm_domain* dom);
+int32_t lbm_batch_size(const lbm_batch* b);
+
+/* Advance every member nsteps time steps (Eqs. 6 and 11 with all boundary
+ * rules), one launch per step, asynchronously on the batch's stream. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* One check interval of the steady-state loop for every member:
+ * check_every - 1 plain steps, then one step with the fused FP64 observables
+ * and residual against each member's previous snapshot (-1 on a member's
+ * first check).  Synchronises the batch's stream; each member's observables
+ * are then available from lbm_last_observables. */
+lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every);
+
+/* Observables of the domain's last batch check (EINVAL if none). */
+lbm_status lbm_last_observables(const lbm_domain* dom, lbm_observables* out);
+
+/* Launch shape of the batch (switches every member). */
+lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_launch* launch);
+lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_launch* launch);
+
+/* Autotuner: time a fixed set of candidate shapes (tile width, rows per
+ * thread, persistent grids) for steps_per_candidate steps each on the current
+ * members, keep the fastest and report it in *chosen (may be NULL).  The timed
+ * steps are real steps of the members. */
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, lbm_launch* chosen);
+
+/* Algorithmic bytes of one batch step (sum of lbm_step_bytes of the members)
+ * and the number of active cells updated per step. */
+double lbm_batch_step_bytes(const lbm_batch* b);
+int64_t lbm_batch_active_cells(const lbm_batch* b);
+
+/* Destroy the batch (members become stand-alone domains again). */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* ---- observables without caller-provided reduction scratch ----------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * may not allocate device memory once they are running, for instance a host

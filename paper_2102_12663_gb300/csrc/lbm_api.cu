@@ -123,6 +123,11 @@ struct lbm_domain {
     bool have_params = false;
     int64_t step = 0;
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
+    std::vector<int4> htiles;         // host copy of the tile list
+    lbm_batch* batch = nullptr;       // batch this domain belongs to, if any
+    cudaStream_t own_stream = nullptr;
+    lbm_observables last_obs{};       // observables of the last batch check
+    bool have_last_obs = false;
 };
 
 // plain steps captured per CUDA graph (even, so a replay returns to the same parity)
@@ -164,6 +169,7 @@ static lbm_status build_tiles(lbm_domain* d) {
     d->ntiles = (int)tiles.size();
     d->tiled_cells = cells;
     d->h.ntiles = d->ntiles;
+    d->htiles = tiles;
     if (!tiles.empty())
         CK(cudaMemcpyAsync(d->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, d->stream));
@@ -464,8 +470,11 @@ static void drop_graph(lbm_domain* d) {
     d->graph = nullptr;
 }
 
+extern "C" lbm_status lbm_batch_remove(lbm_batch* b, lbm_domain* d);
+
 extern "C" void lbm_destroy_domain(lbm_domain* d) {
     if (!d) return;
+    if (d->batch) lbm_batch_remove(d->batch, d);
     cudaStreamSynchronize(d->stream);
     drop_graph(d);
     delete d;
@@ -837,3 +846,330 @@ void fill_observables(const lbm_domain* d, const double* o, lbm_observables* out
     fill_obs(d, o, d->step, out);
 }
 }  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// batches: many domains advanced by one launch per step over a merged tile list
+
+static constexpr int BATCH_GRAPH_STEPS = 32;
+
+struct lbm_batch {
+    int prec = 0;
+    int max_inst = 0;
+    int64_t max_tiles = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    char* base = nullptr;
+    InstDesc* d_table = nullptr;
+    double* d_obs = nullptr;
+    int4* d_tiles = nullptr;
+    std::vector<lbm_domain*> members;  // table order
+    std::vector<InstDesc> htable;
+    std::vector<double> hobs;
+    lbm_launch launch{128, 1, 2, 0};
+    int ntiles = 0;
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+};
+
+struct BatchLayout {
+    size_t table, obs, tiles, total;
+};
+
+static BatchLayout batch_layout(int max_inst, int64_t max_tiles) {
+    BatchLayout L;
+    size_t off = 0;
+    L.table = off; off = align_up(off + (size_t)max_inst * sizeof(InstDesc));
+    L.obs = off; off = align_up(off + (size_t)max_inst * NOBS * sizeof(double));
+    L.tiles = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
+    L.total = off;
+    return L;
+}
+
+extern "C" size_t lbm_batch_bytes(int32_t max_instances, int64_t max_tiles) {
+    if (max_instances <= 0 || max_tiles <= 0 || max_tiles > INT32_MAX) return 0;
+    return batch_layout(max_instances, max_tiles).total;
+}
+
+extern "C" lbm_status lbm_batch_create(int32_t precision, int32_t max_instances, int64_t max_tiles,
+                                       const lbm_launch* launch, void* dev_buf, size_t bytes,
+                                       void* stream, lbm_batch** out) {
+    if (!out) return fail(LBM_EINVAL, "null argument");
+    *out = nullptr;
+    if (!store_size(precision)) return fail(LBM_EINVAL, "unknown precision %d", precision);
+    if (max_instances <= 0 || max_tiles <= 0 || max_tiles > INT32_MAX)
+        return fail(LBM_EINVAL, "bad batch capacity");
+    if (launch && !launch_ok(*launch)) return fail(LBM_EINVAL, "invalid launch shape");
+    const BatchLayout L = batch_layout(max_instances, max_tiles);
+    if (!dev_buf || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_buf) % ALIGN) != 0)
+        return fail(LBM_ENOMEM, "batch buffer too small or not 256-byte aligned (need %zu bytes)", L.total);
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return fail(LBM_ENOMEM, "host allocation failed");
+    b->prec = precision;
+    b->max_inst = max_instances;
+    b->max_tiles = max_tiles;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->base = static_cast<char*>(dev_buf);
+    b->d_table = reinterpret_cast<InstDesc*>(b->base + L.table);
+    b->d_obs = reinterpret_cast<double*>(b->base + L.obs);
+    b->d_tiles = reinterpret_cast<int4*>(b->base + L.tiles);
+    if (launch) b->launch = *launch;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+static void batch_drop_graph(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+extern "C" lbm_status lbm_batch_add(lbm_batch* b, lbm_domain* d) {
+    if (!b || !d) return fail(LBM_EINVAL, "null argument");
+    if (d->batch) return fail(LBM_EBUSY, "domain already belongs to a batch");
+    if (d->prec != b->prec) return fail(LBM_EINVAL, "domain precision differs from the batch's");
+    if (!d->have_params) return fail(LBM_EINVAL, "set the domain's parameters before adding it");
+    if ((int)b->members.size() >= b->max_inst) return fail(LBM_EBUSY, "batch is full");
+    lbm_status st;
+    if (std::memcmp(&d->launch, &b->launch, sizeof(lbm_launch)) != 0 &&
+        (st = lbm_set_launch(d, &b->launch)) != LBM_OK)
+        return st;
+    int64_t total = d->ntiles;
+    for (lbm_domain* m : b->members) total += m->ntiles;
+    if (total > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded (%lld tiles)", (long long)total);
+    CK(cudaStreamSynchronize(d->stream));  // order the domain's earlier work before the batch's
+    d->own_stream = d->stream;
+    d->stream = b->stream;
+    d->batch = b;
+    b->members.push_back(d);
+    b->dirty = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_remove(lbm_batch* b, lbm_domain* d) {
+    if (!b || !d) return fail(LBM_EINVAL, "null argument");
+    auto it = std::find(b->members.begin(), b->members.end(), d);
+    if (it == b->members.end()) return fail(LBM_EINVAL, "domain is not a member of this batch");
+    CK(cudaStreamSynchronize(b->stream));
+    b->members.erase(it);
+    d->stream = d->own_stream;
+    d->batch = nullptr;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+extern "C" int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->members.size() : -1; }
+
+// merged tile list: member k's local tile t becomes (k, t, x0, y0)
+static lbm_status batch_rebuild(lbm_batch* b) {
+    if (!b->dirty) return LBM_OK;
+    std::vector<int4> tiles;
+    for (size_t k = 0; k < b->members.size(); ++k)
+        for (const int4& t : b->members[k]->htiles) tiles.push_back(make_int4((int)k, t.y, t.z, t.w));
+    if ((int64_t)tiles.size() > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded");
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                           b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->ntiles = (int)tiles.size();
+    batch_drop_graph(b);
+    b->dirty = false;
+    return LBM_OK;
+}
+
+// table entry k = member k's descriptor with its current step parity and a
+// slot of the batch's contiguous observables array
+static lbm_status batch_upload_table(lbm_batch* b) {
+    b->htable.resize(b->members.size());
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        InstDesc t = b->members[k]->h;
+        t.parity = (int)(b->members[k]->step & 1);
+        t.obs = b->d_obs + k * NOBS;
+        b->htable[k] = t;
+    }
+    if (!b->htable.empty())
+        CK(cudaMemcpyAsync(b->d_table, b->htable.data(), b->htable.size() * sizeof(InstDesc),
+                           cudaMemcpyHostToDevice, b->stream));
+    return LBM_OK;
+}
+
+static int batch_grid(const lbm_batch* b) {
+    if (b->launch.blocks_per_sm <= 0) return std::max(b->ntiles, 1);
+    return std::max(1, std::min(b->ntiles, b->launch.blocks_per_sm * b->num_sms));
+}
+
+static lbm_status batch_ensure_graph(lbm_batch* b) {
+    if (b->graph) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    const Shape sh = shape_of(b->launch);
+    const int grid = batch_grid(b);
+    cudaGraphNode_t prev = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < BATCH_GRAPH_STEPS && e == cudaSuccess; ++k) {
+        const InstDesc* a0 = b->d_table;
+        const int4* a1 = b->d_tiles;
+        int a2 = b->ntiles, a3 = k & 1, a4 = 0;
+        Shape a5 = sh;
+        void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(step_fn(b->prec, false));
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(sh.tw, sh.bh);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(LBM_ECUDA, "batch graph construction failed: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    if (b->members.empty() || nsteps == 0) return LBM_OK;
+    lbm_status st;
+    if ((st = batch_rebuild(b)) != LBM_OK || (st = batch_upload_table(b)) != LBM_OK) return st;
+    int64_t k = 0;
+    if (nsteps >= BATCH_GRAPH_STEPS && b->ntiles > 0) {
+        if ((st = batch_ensure_graph(b)) != LBM_OK) return st;
+        for (; nsteps - k >= BATCH_GRAPH_STEPS; k += BATCH_GRAPH_STEPS)
+            CK(cudaGraphLaunch(b->graph, b->stream));
+    }
+    for (; k < nsteps; ++k)
+        CK(launch_step(b->prec, b->d_table, b->d_tiles, b->ntiles, (int)(k & 1), 0,
+                       shape_of(b->launch), batch_grid(b), b->stream));
+    for (lbm_domain* m : b->members) m->step += nsteps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (b->members.empty()) return LBM_OK;
+    lbm_status st;
+    if ((st = lbm_batch_step(b, check_every - 1)) != LBM_OK) return st;
+    if ((st = batch_rebuild(b)) != LBM_OK || (st = batch_upload_table(b)) != LBM_OK) return st;
+    CK(launch_step(b->prec, b->d_table, b->d_tiles, b->ntiles, 0,
+                   OBS_STATS | OBS_SNAP | OBS_WRITE | OBS_RESID, shape_of(b->launch), batch_grid(b),
+                   b->stream));
+    for (lbm_domain* m : b->members) m->step += 1;
+    const int n = (int)b->members.size();
+    CK(launch_finalize(b->d_table, n, b->stream));
+    b->hobs.resize((size_t)n * NOBS);
+    CK(cudaMemcpyAsync(b->hobs.data(), b->d_obs, b->hobs.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < n; ++k) {
+        lbm_domain* m = b->members[k];
+        // the observing step ran at step - 1 (pre-collision state of that step)
+        fill_obs(m, b->hobs.data() + (size_t)k * NOBS, m->step - 1, &m->last_obs);
+        m->have_last_obs = true;
+        if (!m->h.snap_valid) {
+            m->h.snap_valid = 1;
+            if ((st = upload_desc(m)) != LBM_OK) return st;
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_last_observables(const lbm_domain* d, lbm_observables* out) {
+    if (!d || !out) return fail(LBM_EINVAL, "null argument");
+    if (!d->have_last_obs) return fail(LBM_EINVAL, "no batch check has observed this domain yet");
+    *out = d->last_obs;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_launch* l) {
+    if (!b || !l) return fail(LBM_EINVAL, "null argument");
+    *l = b->launch;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_launch* l) {
+    if (!b || !l) return fail(LBM_EINVAL, "null argument");
+    if (!launch_ok(*l)) return fail(LBM_EINVAL, "invalid launch shape");
+    int64_t total = 0;
+    for (lbm_domain* m : b->members) {
+        lbm_status st = lbm_set_launch(m, l);
+        if (st != LBM_OK) return st;
+        total += m->ntiles;
+    }
+    if (total > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded for this shape");
+    b->launch = *l;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+extern "C" double lbm_batch_step_bytes(const lbm_batch* b) {
+    if (!b) return 0.0;
+    double s = 0.0;
+    for (const lbm_domain* m : b->members) s += lbm_step_bytes(m);
+    return s;
+}
+
+extern "C" int64_t lbm_batch_active_cells(const lbm_batch* b) {
+    if (!b) return -1;
+    int64_t s = 0;
+    for (const lbm_domain* m : b->members) s += m->info.n_active;
+    return s;
+}
+
+// Autotuner: time each candidate shape on the current members (the timed
+// steps are real steps of the members) and keep the fastest.
+extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, lbm_launch* chosen) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (steps_per_candidate < 2) return fail(LBM_EINVAL, "steps_per_candidate must be >= 2");
+    if (b->members.empty()) return fail(LBM_EINVAL, "empty batch");
+    static const lbm_launch cand[] = {
+        {64, 1, 4, 0}, {128, 1, 4, 0}, {32, 2, 4, 0}, {128, 1, 2, 0}, {64, 2, 2, 0},
+        {64, 1, 8, 0}, {256, 1, 2, 0}, {64, 1, 4, 16}, {128, 1, 2, 8}, {32, 4, 2, 0}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    lbm_launch best = b->launch;
+    lbm_status st = LBM_OK;
+    for (const lbm_launch& c : cand) {
+        if ((st = lbm_batch_set_launch(b, &c)) != LBM_OK) {
+            if (st == LBM_EBUSY) { st = LBM_OK; continue; }  // shape needs more tiles than fit
+            break;
+        }
+        if ((st = lbm_batch_step(b, 2)) != LBM_OK) break;  // warm-up, builds the tile list
+        cudaEventRecord(e0, b->stream);
+        if ((st = lbm_batch_step(b, steps_per_candidate)) != LBM_OK) break;
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    if ((st = lbm_batch_set_launch(b, &best)) != LBM_OK) return st;
+    if (chosen) *chosen = best;
+    return LBM_OK;
+}
+
+extern "C" void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (lbm_domain* m : b->members) {
+        m->stream = m->own_stream;
+        m->batch = nullptr;
+    }
+    batch_drop_graph(b);
+    delete b;
+}

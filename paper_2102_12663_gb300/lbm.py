@@ -129,6 +129,20 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "lbm_get_tile_count": (i64, [dom]),
         "lbm_step_bytes": (dbl, [dom]),
         "lbm_destroy_domain": (None, [dom]),
+        "lbm_batch_bytes": (sz, [i32, i64]),
+        "lbm_batch_create": (i32, [i32, i32, i64, P(Launch), vp, sz, vp, P(vp)]),
+        "lbm_batch_add": (i32, [vp, dom]),
+        "lbm_batch_remove": (i32, [vp, dom]),
+        "lbm_batch_size": (i32, [vp]),
+        "lbm_batch_step": (i32, [vp, i64]),
+        "lbm_batch_check": (i32, [vp, i32]),
+        "lbm_last_observables": (i32, [dom, P(Observables)]),
+        "lbm_batch_set_launch": (i32, [vp, P(Launch)]),
+        "lbm_batch_get_launch": (i32, [vp, P(Launch)]),
+        "lbm_batch_tune": (i32, [vp, i32, P(Launch)]),
+        "lbm_batch_step_bytes": (dbl, [vp]),
+        "lbm_batch_active_cells": (i64, [vp]),
+        "lbm_batch_destroy": (None, [vp]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -295,6 +309,12 @@ class Domain:
         check(self._L.lbm_read_observables_noalloc(self._h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in Observables._fields_}
 
+    def last_observables(self) -> dict:
+        """Observables of the last batch check of this domain."""
+        o = Observables()
+        check(self._L.lbm_last_observables(self._h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Observables._fields_}
+
     def fields(self):
         """(u[2, ny, nx], p[ny, nx], T[ny, nx]) float64 device tensors."""
         torch = _torch()
@@ -352,3 +372,78 @@ class Domain:
 
     def step_bytes(self) -> float:
         return float(self._L.lbm_step_bytes(self._h))
+
+
+def _launch_dict(l: Launch) -> dict:
+    return {k: getattr(l, k) for k, _ in Launch._fields_}
+
+
+class Batch:
+    """Many domains of one precision advanced by one launch per time step."""
+
+    def __init__(self, precision="f32", max_instances=64, max_tiles=1 << 20, launch=None,
+                 device=None, stream=None):
+        torch = _torch()
+        L = load()
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = int(L.lbm_batch_bytes(int(max_instances), int(max_tiles)))
+        if nbytes == 0:
+            raise LBMError(EINVAL, "invalid batch capacity")
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        lp = ctypes.byref(Launch(**launch)) if launch else None
+        h = ctypes.c_void_p()
+        check(L.lbm_batch_create(self.precision, int(max_instances), int(max_tiles), lp,
+                                 ctypes.c_void_p(self.buf.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h, self._L = h, L
+        self.members = []
+
+    def add(self, dom: Domain):
+        check(self._L.lbm_batch_add(self._h, dom.handle))
+        self.members.append(dom)
+
+    def remove(self, dom: Domain):
+        check(self._L.lbm_batch_remove(self._h, dom.handle))
+        self.members.remove(dom)
+
+    def __len__(self):
+        return int(self._L.lbm_batch_size(self._h))
+
+    def step(self, n: int = 1):
+        check(self._L.lbm_batch_step(self._h, int(n)))
+
+    def check(self, check_every: int = 100):
+        check(self._L.lbm_batch_check(self._h, int(check_every)))
+
+    def set_launch(self, **launch):
+        check(self._L.lbm_batch_set_launch(self._h, ctypes.byref(Launch(**launch))))
+
+    def get_launch(self) -> dict:
+        l = Launch()
+        check(self._L.lbm_batch_get_launch(self._h, ctypes.byref(l)))
+        return _launch_dict(l)
+
+    def tune(self, steps_per_candidate: int = 20) -> dict:
+        l = Launch()
+        check(self._L.lbm_batch_tune(self._h, int(steps_per_candidate), ctypes.byref(l)))
+        return _launch_dict(l)
+
+    def step_bytes(self) -> float:
+        return float(self._L.lbm_batch_step_bytes(self._h))
+
+    def active_cells(self) -> int:
+        return int(self._L.lbm_batch_active_cells(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.lbm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,227 @@
+"""Continuous-batching server of steady-state eye solves.
+
+Requests (a grid size, a chamber angle, lattice parameters and a storage
+precision) arrive over time.  Each one is admitted as soon as its device
+memory fits the HBM budget and its precision's batch has a free slot.  Its
+populations then stay resident, and it advances with every other admitted
+request of that precision in one fused launch per time step (lbm_batch_*).
+Every tick runs one check interval of the steady-state loop for all members.
+A member whose residual max |du| over the interval falls below tol, that hits
+the step cap, or whose pressure turned NaN is retired: its observables are
+read, its memory is released, and waiting requests take its place.  Work of
+requests that arrive while others run overlaps on the device inside the
+shared launches.
+
+``solve_one_at_a_time`` is the plain baseline: every request on its own FP32
+domain, one after the other, through lbm_run_to_steady.
+
+This module only orchestrates; every step of every solve runs in the CUDA
+library.
+"""
+from __future__ import annotations
+
+import dataclasses
+import statistics
+import time
+
+from . import lbm
+
+
+@dataclasses.dataclass
+class Request:
+    id: int
+    nx: int
+    ny: int
+    angle_deg: float
+    params: dict
+    precision: str = "f32"
+    arrival_s: float = 0.0
+
+
+@dataclasses.dataclass
+class Result:
+    id: int
+    precision: str
+    nx: int
+    ny: int
+    steps: int
+    converged: bool
+    unstable: bool
+    observables: dict
+    arrival_s: float
+    admit_s: float
+    finish_s: float
+
+    @property
+    def latency_s(self) -> float:
+        return self.finish_s - self.arrival_s
+
+
+def requests_from_draws(draws) -> list:
+    """Requests from workloads.request_stream / batch_instances draws."""
+    out = []
+    for d in draws:
+        out.append(Request(id=d["id"], nx=d["nx"], ny=d["ny"], angle_deg=d["angle_deg"],
+                           params=d["params"], precision="f16" if d.get("fp16") else "f32",
+                           arrival_s=d.get("arrival_s", 0.0)))
+    return out
+
+
+def domain_bytes(req: Request) -> int:
+    import ctypes
+    L = lbm.load()
+    g, _ = lbm.geometry_desc(dict(nx=req.nx, ny=req.ny, angle_deg=req.angle_deg))
+    return int(L.lbm_domain_bytes(ctypes.byref(g), lbm.PRECISIONS[req.precision]))
+
+
+class Server:
+    def __init__(self, budget_bytes: float = 150e9, tol: float = 1e-7, check_every: int = 100,
+                 max_steps: int = 20000, max_instances: int = 64, max_tiles: int = 1 << 21,
+                 launch: dict | None = None, autotune: bool = False, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.budget = float(budget_bytes)
+        self.tol, self.check_every, self.max_steps = tol, int(check_every), int(max_steps)
+        self.max_instances, self.max_tiles = int(max_instances), int(max_tiles)
+        self.launch = launch or dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0)
+        self.autotune = autotune
+        self.batches = {}
+        self.active = {}  # id -> (request, domain, bytes, admit time)
+        self.used = 0
+        self.peak_used = 0
+        self.results = []
+        self.ticks = 0
+        self.cell_updates = 0
+
+    def _batch(self, precision: str):
+        if precision not in self.batches:
+            self.batches[precision] = lbm.Batch(precision, self.max_instances, self.max_tiles,
+                                                launch=self.launch, device=self.device,
+                                                stream=self.stream)
+        return self.batches[precision]
+
+    def fits(self, req: Request) -> bool:
+        b = self.batches.get(req.precision)
+        room = b is None or len(b) < self.max_instances
+        return room and self.used + domain_bytes(req) <= self.budget
+
+    def admit(self, req: Request, now: float):
+        nbytes = domain_bytes(req)
+        with self.torch.cuda.stream(self.stream):
+            dom = lbm.Domain(dict(nx=req.nx, ny=req.ny, angle_deg=req.angle_deg),
+                             precision=req.precision, device=self.device, stream=self.stream)
+            dom.set_launch(**self.launch)
+            dom.set_params(req.params)
+        self._batch(req.precision).add(dom)
+        self.active[req.id] = (req, dom, nbytes, now)
+        self.used += nbytes
+        self.peak_used = max(self.peak_used, self.used)
+
+    def tick(self, now_fn):
+        """One check interval for every batch; retire finished members."""
+        for prec, b in self.batches.items():
+            if len(b) == 0:
+                continue
+            if self.autotune and not getattr(b, "_tuned", False) and len(b) >= 4:
+                b.tune(steps_per_candidate=8)
+                self.launch = b.get_launch()
+                b._tuned = True
+            self.cell_updates += b.active_cells() * self.check_every
+            b.check(self.check_every)
+        self.ticks += 1
+        t = now_fn()
+        for rid in list(self.active):
+            req, dom, nbytes, t_admit = self.active[rid]
+            o = dom.last_observables()
+            converged = 0.0 <= o["residual"] < self.tol
+            unstable = bool(o["nan_flag"])
+            if converged or unstable or dom.step_count >= self.max_steps:
+                b = self.batches[req.precision]
+                b.remove(dom)
+                self.results.append(Result(req.id, req.precision, req.nx, req.ny, dom.step_count,
+                                           converged, unstable, o, req.arrival_s, t_admit, t))
+                dom.close()
+                del self.active[rid]
+                self.used -= nbytes
+
+    def run(self, requests, realtime: bool = True) -> list:
+        """Serve `requests`; arrival times are honoured against the wall clock
+        when realtime is set (else every request is present at t = 0)."""
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        t0 = time.perf_counter()
+        now = (lambda: time.perf_counter() - t0) if realtime else (lambda: time.perf_counter() - t0)
+        arrivals = {r.id: (r.arrival_s if realtime else 0.0) for r in pending}
+        for r in pending:
+            r.arrival_s = arrivals[r.id]
+        while pending or self.active:
+            t = now()
+            while pending and pending[0].arrival_s <= t and self.fits(pending[0]):
+                self.admit(pending.pop(0), t)
+            if not self.active:
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival_s - now(), 0.05)))
+                continue
+            self.tick(now)
+        self.wall_s = now()
+        return self.results
+
+    def close(self):
+        for _, dom, _, _ in self.active.values():
+            dom.close()
+        self.active.clear()
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()
+
+
+def solve_one_at_a_time(requests, tol: float = 1e-7, check_every: int = 100,
+                        max_steps: int = 20000, launch: dict | None = None, device=None,
+                        realtime: bool = True, precision: str = "f32") -> list:
+    """Baseline: each request alone on a plain FP32 domain, in arrival order."""
+    import torch
+    dev = torch.device(device if device is not None else "cuda")
+    stream = torch.cuda.Stream(device=dev)
+    launch = launch or dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0)
+    t0 = time.perf_counter()
+    out = []
+    for r in sorted(requests, key=lambda q: q.arrival_s):
+        arrival = r.arrival_s if realtime else 0.0
+        wait = arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        t_start = time.perf_counter() - t0
+        with torch.cuda.stream(stream):
+            dom = lbm.Domain(dict(nx=r.nx, ny=r.ny, angle_deg=r.angle_deg), precision=precision,
+                             device=dev, stream=stream)
+            dom.set_launch(**launch)
+            dom.set_params(r.params)
+            try:
+                st, steps = dom.run_to_steady(tol, check_every=check_every, max_steps=max_steps)
+                unstable = False
+            except lbm.LBMError as e:
+                if e.status != lbm.EUNSTABLE:
+                    raise
+                st, steps, unstable = e.status, dom.step_count, True
+            o = dom.observables()
+            dom.close()
+        out.append(Result(r.id, precision, r.nx, r.ny, steps, st == lbm.OK, unstable, o, arrival,
+                          t_start, time.perf_counter() - t0))
+    return out
+
+
+def summary(results, wall_s: float) -> dict:
+    lat = sorted(r.latency_s for r in results)
+    def pct(q):
+        if not lat:
+            return None
+        k = min(len(lat) - 1, max(0, int(round(q * (len(lat) - 1)))))
+        return lat[k]
+    return {"solves": len(results), "wall_s": wall_s,
+            "solves_per_s": len(results) / wall_s if wall_s > 0 else None,
+            "p50_s": pct(0.50), "p99_s": pct(0.99),
+            "converged": sum(r.converged for r in results),
+            "capped": sum((not r.converged) and (not r.unstable) for r in results),
+            "unstable": sum(r.unstable for r in results),
+            "mean_steps": statistics.mean(r.steps for r in results) if results else None}

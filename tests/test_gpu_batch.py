@@ -1,0 +1,140 @@
+"""Batched stepping: many uneven eye instances advanced by one launch per
+step over a merged tile list.  A member's results must not depend on the
+batch it runs in (bitwise), must match the FP64 oracle, and the autotuner's
+pick must not change them."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2102_12663_gb300 import lbm
+from paper_2102_12663_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lbm.load(build_if_missing=True)
+
+
+def make(inst, prec):
+    dom = lbm.Domain(dict(nx=inst["nx"], ny=inst["ny"], angle_deg=inst["angle_deg"]), precision=prec)
+    dom.set_launch(**SHAPE)
+    dom.set_params(inst["params"])
+    return dom
+
+
+def small_instances(n, seed=7):
+    return W.batch_instances(n, seed=seed, ny_lo=48, ny_hi=112)
+
+
+def pops(dom):
+    f, g = dom.populations()
+    torch.cuda.synchronize()
+    return f.cpu().numpy().reshape(9, -1), g.cpu().numpy().reshape(4, -1)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_alone_equals_in_mix_bitwise(prec):
+    inst = small_instances(5)
+    alone = make(inst[0], prec)
+    b1 = lbm.Batch(prec, max_instances=1, max_tiles=1 << 14, launch=SHAPE)
+    b1.add(alone)
+    mixed = [make(i, prec) for i in inst]
+    b5 = lbm.Batch(prec, max_instances=8, max_tiles=1 << 16, launch=SHAPE)
+    for d in mixed:
+        b5.add(d)
+    for _ in range(3):
+        b1.check(100)
+        b5.check(100)
+    fa, ga = pops(alone)
+    fm, gm = pops(mixed[0])
+    assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+    oa, om = alone.last_observables(), mixed[0].last_observables()
+    assert oa == om
+    assert oa["step"] == 299 and oa["residual"] >= 0.0
+    b1.close()
+    b5.close()
+
+
+def test_batch_matches_oracle_with_mixed_parity():
+    """Members of different sizes, parameters and step parities (one was
+    stepped alone an odd number of times before joining) against the oracle."""
+    inst = small_instances(3, seed=11)
+    doms = [make(i, "f64") for i in inst]
+    refs = []
+    for i in inst:
+        m, g = O.eye_mask(i["nx"], i["ny"], i["angle_deg"])
+        refs.append(O.State(g, O.make_params(**i["params"]), m))
+    doms[1].step(3)
+    refs[1].run(3)
+    b = lbm.Batch("f64", max_instances=4, max_tiles=1 << 16, launch=SHAPE)
+    for d in doms:
+        b.add(d)
+    b.step(45)
+    b.check(20)
+    for d, r in zip(doms, refs):
+        r.run(65)
+        assert d.step_count == r.step_count
+        f, g = pops(d)
+        assert np.abs(f - r.f).max() <= 1e-12 * np.abs(r.f).max()
+        assert np.abs(g - r.T).max() <= 1e-12 * np.abs(r.T).max()
+    # the observables of the check step (step 64 for the even members)
+    o = doms[0].last_observables()
+    r0 = O.State(O.eye_mask(inst[0]["nx"], inst[0]["ny"], inst[0]["angle_deg"])[1],
+                 O.make_params(**inst[0]["params"]),
+                 O.eye_mask(inst[0]["nx"], inst[0]["ny"], inst[0]["angle_deg"])[0])
+    r0.run(64)
+    oo = r0.observe()
+    assert o["step"] == 64
+    assert o["iop"] == pytest.approx(oo["iop"], rel=1e-12)
+    assert o["wss_cornea"] == pytest.approx(oo["wss_cornea"], rel=1e-12)
+    assert o["mass"] == pytest.approx(oo["mass"], rel=1e-12)
+    # removal hands the domain back; it keeps stepping alone
+    b.remove(doms[2])
+    doms[2].step(5)
+    refs[2].run(5)
+    f, g = pops(doms[2])
+    assert np.abs(f - refs[2].f).max() <= 1e-12 * np.abs(refs[2].f).max()
+    b.close()
+
+
+def test_autotuner_keeps_results():
+    inst = small_instances(4, seed=3)
+    doms = [make(i, "f64") for i in inst]
+    refs = []
+    for i in inst:
+        m, g = O.eye_mask(i["nx"], i["ny"], i["angle_deg"])
+        refs.append(O.State(g, O.make_params(**i["params"]), m))
+    b = lbm.Batch("f64", max_instances=4, max_tiles=1 << 16, launch=SHAPE)
+    for d in doms:
+        b.add(d)
+    chosen = b.tune(steps_per_candidate=4)
+    assert chosen == b.get_launch()
+    n = doms[0].step_count
+    b.step(33)
+    for d, r in zip(doms, refs):
+        r.run(n + 33)
+        f, g = pops(d)
+        assert np.abs(f - r.f).max() <= 1e-12 * np.abs(r.f).max()
+    b.close()
+
+
+def test_batch_capacity_errors():
+    inst = small_instances(2, seed=5)
+    doms = [make(i, "f32") for i in inst]
+    b = lbm.Batch("f32", max_instances=1, max_tiles=1 << 14, launch=SHAPE)
+    b.add(doms[0])
+    with pytest.raises(lbm.LBMError) as e:
+        b.add(doms[1])
+    assert e.value.status == lbm.EBUSY
+    d64 = make(inst[1], "f64")
+    b2 = lbm.Batch("f32", max_instances=2, max_tiles=1 << 14, launch=SHAPE)
+    with pytest.raises(lbm.LBMError) as e:
+        b2.add(d64)
+    assert e.value.status == lbm.EINVAL
+    b.close()
+    b2.close()
