@@ -119,6 +119,23 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max_over_ranks(values, device=None):
+    """Element-wise maximum over every rank of the default process group (NCCL
+    between GPUs, gloo on the host)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def weak_scaling_mlups(active_cells: int, bench_steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job MLUPS: every rank updates its own replica of the workload, so
+    the units processed are world x cells x 100 x bench steps, divided by the
+    slowest rank's time."""
+    return active_cells * CHECK * bench_steps * world / (t_max_ms * 1e-3) / 1e6
+
+
 def eye_params():
     from paper_2102_12663_gb300 import workloads as W
     return W.config_params(W.CONFIG_FP32)
@@ -248,12 +265,9 @@ def run_gpu(args):
 
     t_max = total_ms
     if world > 1:
-        t = torch.tensor([total_ms, e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_s = float(t[0]), float(t[1])
-    updates = n_active * CHECK * args.steps * world
-    value = updates / (t_max * 1e-3) / 1e6
-    e2e_value = updates / e2e_s / 1e6
+        t_max, e2e_s = reduce_max_over_ranks([total_ms, e2e_s], device=dev)
+    value = weak_scaling_mlups(n_active, args.steps, world, t_max)
+    e2e_value = weak_scaling_mlups(n_active, args.steps, world, e2e_s * 1e3)
     peak, peak_kind = hbm_peak()
     achieved = step_bytes / (kernel_ms * 1e-3) / 1e9
     traffic = None
@@ -300,7 +314,228 @@ def run_gpu(args):
     return 0
 
 
-LAUNCH = dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0)
+LAUNCH = dict(tile_w=128, block_rows=2, rows_per_thread=2, blocks_per_sm=0)
+
+
+def _time_intervals(dom_or_batch, n, batch=False):
+    """Device time (ms) of n steady-loop check intervals (100 steps each)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = dom_or_batch.stream
+    e0.record(s)
+    for _ in range(n):
+        if batch:
+            dom_or_batch.check(CHECK)
+        else:
+            dom_or_batch.run_to_steady(0.0, check_every=CHECK, max_steps=CHECK)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_precision(args):
+    """Reduced-storage precision: FP16 / BF16 deviation storage (FP32
+    arithmetic, FP64 reductions) on the 8192 x 4096 eye (throughput), and the
+    error of the steady-loop observables on the 1024 x 512 eye against the
+    FP64 path (itself checked against the FP64 oracle)."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2102_12663_gb300 import lbm
+    from paper_2102_12663_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    lbm.load(build_if_missing=True)
+    cfg = W.CONFIG_PRECISION
+    peak, peak_kind = hbm_peak()
+    thr = {}
+    for prec in ("f16", "bf16", "f32"):
+        st = torch.cuda.Stream()
+        dom = lbm.Domain(dict(nx=cfg["nx"], ny=cfg["ny"], angle_deg=cfg["angle_deg"]),
+                         precision=prec, stream=st)
+        dom.set_launch(**LAUNCH)
+        dom.set_params(W.config_params(cfg))
+        with torch.cuda.stream(st):
+            _time_intervals(dom, 3)
+            ms = _time_intervals(dom, args.intervals)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            dom.step(200)
+            e1.record(st)
+            e1.synchronize()
+            kms = e0.elapsed_time(e1) / 200
+        n_act = dom.info()["n_active"]
+        thr[prec] = {"mlups": n_act * CHECK * args.intervals / (ms * 1e-3) / 1e6,
+                     "kernel_us": kms * 1e3,
+                     "gbs": dom.step_bytes() / (kms * 1e-3) / 1e9,
+                     "hbm_frac": dom.step_bytes() / (kms * 1e-3) / 1e9 / peak,
+                     "bytes_per_cell": dom.step_bytes() / n_act}
+        dom.close()
+        del dom
+        torch.cuda.empty_cache()
+    # error study on the 1024 x 512 eye.  The FP64 run goes to the steady
+    # criterion on u and then on until the pressure level (IOP, which relaxes
+    # on a slower mode than u) changes by less than 1e-8 relative per 20,000
+    # steps; every other precision then runs exactly as many steps.
+    nx, ny = cfg["check_nx"], cfg["check_ny"]
+    pp = W.config_params(cfg, ny=ny)
+    cap = args.error_steps
+    obs = {}
+    total = None
+    for prec in ("f64", "f32", "f16", "bf16"):
+        dom = lbm.Domain(dict(nx=nx, ny=ny, angle_deg=cfg["angle_deg"]), precision=prec)
+        dom.set_launch(**LAUNCH)
+        dom.set_params(pp)
+        if prec == "f64":
+            # tie the FP64 path to the oracle on this grid
+            m, g = O.eye_mask(nx, ny, cfg["angle_deg"])
+            O.set_threads(os.cpu_count() or 1)
+            ref = O.State(g, O.make_params(**pp), m)
+            ref.run(args.oracle_steps)
+            dom.step(args.oracle_steps)
+            f, _ = dom.populations()
+            oracle_rel = float(np.abs(f.cpu().numpy().reshape(9, -1) - ref.f).max()
+                               / np.abs(ref.f).max())
+            del ref, f
+            dom.reset()
+            status, steps = dom.run_to_steady(cfg["tol"], check_every=cfg["check_every"], max_steps=cap)
+            u_steady = steps
+            iop = dom.observables()["iop"]
+            while steps < cap:
+                dom.step(20000)
+                steps += 20000
+                new = dom.observables()["iop"]
+                if abs(new - iop) <= 1e-8 * abs(new):
+                    break
+                iop = new
+            total = steps
+            st_name = lbm.STATUS_NAMES[status]
+        else:
+            dom.run_to_steady(cfg["tol"], check_every=cfg["check_every"], max_steps=total - 1)
+            dom.step(total - dom.step_count)
+            st_name = "fixed steps"
+        o = dom.observables()
+        obs[prec] = (o, dom.step_count, st_name)
+        dom.close()
+    ref = obs["f64"][0]
+    keys = ("iop", "iop_pa", "peak_speed", "wss_cornea", "wss_iris")
+    errors = {p: {k: abs(o[k] - ref[k]) / abs(ref[k]) for k in keys}
+              for p, (o, _, _) in obs.items() if p != "f64"}
+    line = {"metric": "reduced-storage precision study", "unit": "relative error / MLUPS",
+            "dtype": "f16/bf16 storage, f32 arithmetic, f64 reductions", "data": "synthetic",
+            "config": {"workload": f"throughput: {cfg['nx']}x{cfg['ny']} eye; errors: {nx}x{ny} eye at "
+                                   f"the FP64 steady state (max |du| < {cfg['tol']} per "
+                                   f"{cfg['check_every']} steps, then IOP drift < 1e-8 per 20k "
+                                   f"steps; cap {cap} steps), all precisions at the same step",
+                       "tau": cfg["tau"], "Ra": cfg["Ra"], "K_tm": cfg["K_tm"]},
+            "throughput": thr, "peak_gbs": peak, "peak_kind": peak_kind,
+            "errors_vs_f64": errors,
+            "steps": {p: v[1] for p, v in obs.items()},
+            "status": {p: v[2] for p, v in obs.items()},
+            "f64_u_steady_steps": u_steady,
+            "residual_per_100_steps": {p: v[0]["residual"] for p, v in obs.items()},
+            "f64_reference": {k: ref[k] for k in keys},
+            "f64_vs_oracle_max_rel_population_diff": oracle_rel,
+            "oracle_check_steps": args.oracle_steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """64 uneven eye instances (NY log-uniform 128..1024, seeded parameters)
+    in one batch: one launch per step, graph-replayed, autotuned shape;
+    against the same instances stepped one after the other."""
+    import torch
+
+    from paper_2102_12663_gb300 import lbm
+    from paper_2102_12663_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    lbm.load(build_if_missing=True)
+    st = torch.cuda.Stream()
+    insts = W.batch_instances(64)
+    doms = []
+    for i in insts:
+        d = lbm.Domain(dict(nx=i["nx"], ny=i["ny"], angle_deg=i["angle_deg"]), precision="f32", stream=st)
+        d.set_launch(**LAUNCH)
+        d.set_params(i["params"])
+        doms.append(d)
+    b = lbm.Batch("f32", max_instances=64, max_tiles=1 << 21, launch=LAUNCH, stream=st)
+    for d in doms:
+        b.add(d)
+    with torch.cuda.stream(st):
+        chosen = b.tune(steps_per_candidate=20)
+        _time_intervals(b, 3, batch=True)
+        ms = _time_intervals(b, args.intervals, batch=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.step(128)
+        e1.record(st)
+        e1.synchronize()
+        kms = e0.elapsed_time(e1) / 128
+    cells = b.active_cells()
+    peak, peak_kind = hbm_peak()
+    batched = cells * CHECK * args.intervals / (ms * 1e-3) / 1e6
+    gbs = b.step_bytes() / (kms * 1e-3) / 1e9
+    b.close()
+    # the same instances, one after the other, each alone (plain FP32 loop)
+    n_alone = max(2, args.intervals // 4)
+    tot_ms = 0.0
+    with torch.cuda.stream(st):
+        for d in doms:
+            _time_intervals(d, 1)
+            tot_ms += _time_intervals(d, n_alone)
+    alone = cells * CHECK * n_alone / (tot_ms * 1e-3) / 1e6
+    for d in doms:
+        d.close()
+    line = {"metric": "batched coupled MLUPS (active cells)", "value": batched, "unit": "MLUPS",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 eye instances, NY log-uniform 128..1024, NX = 2 NY, seeded "
+                                   "inflow/K/viscosity/angle/gravity/dT; 100-step check intervals",
+                       "instances": 64, "active_cells": cells, "launch": chosen,
+                       "intervals": args.intervals},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "peak_kind": peak_kind},
+            "one_at_a_time_mlups": alone, "speedup_vs_one_at_a_time": batched / alone,
+            "instance_intervals_per_s": 64 * args.intervals / (ms * 1e-3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream (mean 20/s) of steady-solve requests, NY log-uniform
+    128..2048, FP32 or FP16 storage with p = 1/2, 150 GB HBM budget; steady
+    criterion max |du| < 1e-7 per 100 steps with a step cap."""
+    import torch
+
+    from paper_2102_12663_gb300 import lbm, serve
+    from paper_2102_12663_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    lbm.load(build_if_missing=True)
+    draws = W.request_stream(args.requests, rate_hz=20.0, ny_lo=128, ny_hi=2048, fp16_share=0.5)
+    reqs = serve.requests_from_draws(draws)
+    srv = serve.Server(budget_bytes=150e9, tol=1e-7, check_every=CHECK, max_steps=args.cap,
+                       launch=LAUNCH)
+    res = srv.run(reqs, realtime=True)
+    s_served = serve.summary(res, srv.wall_s)
+    s_served["peak_hbm_bytes"] = srv.peak_used
+    s_served["cell_updates_per_s"] = srv.cell_updates / srv.wall_s
+    srv.close()
+    base = serve.solve_one_at_a_time(serve.requests_from_draws(draws), tol=1e-7, check_every=CHECK,
+                                     max_steps=args.cap, launch=LAUNCH, realtime=True)
+    wall = max(r.finish_s for r in base)
+    s_base = serve.summary(base, wall)
+    line = {"metric": "served steady solves per second", "value": s_served["solves_per_s"],
+            "unit": "solves/s", "higher_is_better": True, "dtype": "f32+f16 storage",
+            "data": "synthetic",
+            "config": {"workload": f"{args.requests} Poisson requests (mean 20/s), NY log-uniform "
+                                   f"128..2048, FP16 storage p=1/2, budget 150 GB, tol 1e-7 per 100 "
+                                   f"steps, cap {args.cap} steps"},
+            "served": s_served, "one_at_a_time_fp32": s_base,
+            "speedup_solves_per_s": s_served["solves_per_s"] / s_base["solves_per_s"],
+            "p50_ratio": s_base["p50_s"] / s_served["p50_s"],
+            "p99_ratio": s_base["p99_s"] / s_served["p99_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
@@ -315,11 +550,27 @@ def main():
                          "workload (no timing, no JSON line) and exit")
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16", "f64"],
                     help="storage precision for --profile")
+    ap.add_argument("--launch", default=None,
+                    help="launch shape for --profile: tile_w,block_rows,rows_per_thread,blocks_per_sm")
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "precision", "batch", "serve"],
+                    help="fp32: the FP32 4096x2048 throughput line (default); precision, batch, "
+                         "serve: the reduced-storage, batching and serving studies")
+    ap.add_argument("--intervals", type=int, default=10, help="timed check intervals (studies)")
+    ap.add_argument("--error-steps", type=int, default=2000000, help="step cap of the error study")
+    ap.add_argument("--oracle-steps", type=int, default=500, help="oracle cross-check steps")
+    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--cap", type=int, default=10000, help="serving: step cap per request")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 
@@ -330,7 +581,11 @@ def run_profile(args):
     from paper_2102_12663_gb300 import lbm
     lbm.load(build_if_missing=True)
     dom = lbm.Domain(dict(nx=NX, ny=NY, angle_deg=45.0), precision=args.precision)
-    dom.set_launch(**LAUNCH)
+    launch = LAUNCH
+    if args.launch:
+        launch = dict(zip(("tile_w", "block_rows", "rows_per_thread", "blocks_per_sm"),
+                          (int(v) for v in args.launch.split(","))))
+    dom.set_launch(**launch)
     dom.set_params(eye_params())
     for _ in range(args.profile):
         dom.step(1)

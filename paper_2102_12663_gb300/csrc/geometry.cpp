@@ -26,7 +26,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 
 namespace lbm {
 

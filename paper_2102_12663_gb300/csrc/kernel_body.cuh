@@ -23,6 +23,13 @@
 
 #include "lbm_internal.cuh"
 
+// Resident blocks of 256 threads the step kernel is compiled for (register
+// budget 65536 / (256 * n)): the two-cell pair path keeps 26 populations and
+// the collision temporaries of two cells live.
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 3
+#endif
+
 namespace lbm {
 
 // Free constants of Eq. 7 (lambda + gamma = sigma, lambda + 2 gamma = 1/2)
@@ -84,23 +91,16 @@ __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPA
     }
 }
 
-template <class ST, bool OBS, int PAR>
-__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode,
-                                            double* acc) {
-    using T = typename ST::T;
-    using R = typename ST::R;
+// neighbour indices of cell (x, y) (wrap-around only ever triggers on
+// periodic edges: a non-periodic edge holds no active cell)
+__device__ __forceinline__ void neighbours(const InstDesc& d, int x, int y, int* nb) {
     const int nx = d.nx, ny = d.ny;
-    const int c = y * nx + x;
-
-    // neighbour indices (wrap-around only ever triggers on periodic edges:
-    // a non-periodic edge holds no active cell)
     const int xl = x == 0 ? nx - 1 : x - 1;
     const int xr = x == nx - 1 ? 0 : x + 1;
     const int yd = (y == 0 ? ny - 1 : y - 1) * nx;
     const int yu = (y == ny - 1 ? 0 : y + 1) * nx;
     const int yc = y * nx;
-    int nb[9];
-    nb[0] = c;
+    nb[0] = yc + x;
     nb[1] = yc + xr;
     nb[2] = yu + x;
     nb[3] = yc + xl;
@@ -109,17 +109,20 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     nb[6] = yu + xl;
     nb[7] = yd + xl;
     nb[8] = yd + xr;
+}
 
-    T* const P = static_cast<T*>(d.pops);
+// Load the mask byte and the 13 populations of cell nb[0] (AA read pattern).
+// The mask and all populations are requested together (every slot index is
+// in range for any cell of the grid), so an active cell pays one memory round
+// trip; a solid cell inside a launched tile discards them.
+template <class ST, int PAR>
+__device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, typename ST::R* f,
+                                          typename ST::R* g, uint8_t& m) {
+    using T = typename ST::T;
+    const T* const P = static_cast<const T*>(d.pops);
     const int np = (int)d.npad;  // 13 * npad < 2^31 (checked at creation)
-    const Phys<R>& ph = phys<R>(d);
-
-    // ---- load (AA read pattern) -------------------------------------------
-    // The mask and all 13 populations are requested together (every slot
-    // index is in range for any cell of the grid), so an active cell pays one
-    // memory round trip; a solid cell inside a launched tile discards them.
-    const uint8_t m = d.mask[c];
-    R f[9], g[4];
+    const int c = nb[0];
+    m = d.mask[c];
     if (PAR == 0) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = ST::ldf(P + i * np + c, d);
@@ -132,6 +135,24 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
 #pragma unroll
         for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + (8 + opp(i)) * np + nb[opp(i)], d);
     }
+}
+
+// Everything after the load: observables, collision, boundary rules, stores.
+template <class ST, bool OBS, int PAR>
+__device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
+                                          const typename ST::R* f, const typename ST::R* g,
+                                          uint8_t m, int mode, double* acc) {
+    using T = typename ST::T;
+    using R = typename ST::R;
+    const int nx = d.nx, ny = d.ny;
+    int nb[9];
+    neighbours(d, x, y, nb);
+    const int c = nb[0];
+    const int xl = x == 0 ? nx - 1 : x - 1;
+    const int xr = x == nx - 1 ? 0 : x + 1;
+    T* const P = static_cast<T*>(d.pops);
+    const int np = (int)d.npad;
+    const Phys<R>& ph = phys<R>(d);
     const int type = m & TYPE_BITS;
     if (type > POROUS) return;
 
@@ -349,8 +370,481 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     }
 }
 
+template <class ST, bool OBS, int PAR>
+__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode, double* acc) {
+    using R = typename ST::R;
+    int nb[9];
+    neighbours(d, x, y, nb);
+    R f[9], g[4];
+    uint8_t m;
+    load_cell<ST, PAR>(d, nb, f, g, m);
+    cell_body<ST, OBS, PAR>(d, x, y, f, g, m, mode, acc);
+}
+
+// Rows of a tile with one cell per thread, software-pipelined: the loads of
+// the thread's next row are issued before the current row is computed, so
+// every thread keeps a cell's worth of loads in flight while it computes.
+// Rows never share a slot (each slot is read and written only by the cell
+// that owns it), so reading the next row before storing this one is exact.
+template <class ST, int PAR>
+__device__ __forceinline__ void tile_rows_pipelined(const InstDesc& sd, const int4& te, int rpt) {
+    using R = typename ST::R;
+    const int x = te.z + threadIdx.x;
+    const bool xin = x < sd.nx;
+    int y = te.w + threadIdx.y;
+    bool ok = xin && y < sd.ny;
+    R f[9], g[4];
+    uint8_t m = ADIABATIC;
+    if (ok) {
+        int nb[9];
+        neighbours(sd, x, y, nb);
+        load_cell<ST, PAR>(sd, nb, f, g, m);
+    }
+    for (int r = 0; r < rpt; ++r) {
+        const int yn = y + blockDim.y;
+        const bool ok2 = r + 1 < rpt && xin && yn < sd.ny;
+        R f2[9], g2[4];
+        uint8_t m2 = ADIABATIC;
+        if (ok2) {
+            int nb[9];
+            neighbours(sd, x, yn, nb);
+            load_cell<ST, PAR>(sd, nb, f2, g2, m2);
+        }
+        if (ok) cell_body<ST, false, PAR>(sd, x, y, f, g, m, 0, nullptr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = f2[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g[i] = g2[i];
+        m = m2;
+        y = yn;
+        ok = ok2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Interior fast path of the FP32-arithmetic kernels: one thread updates two
+// neighbouring cells (x, x+1) of a row, both active and with no boundary
+// neighbour, and every lane of its warp does the same on consecutive pairs of
+// that row.  Populations move as 2-cell vectors.  On an odd step the
+// x-shifted reads and writes are assembled from the neighbouring lane's pair
+// by warp shuffles; the warp's first and last lanes fetch or store the one
+// element that lies outside the warp.  Same model as update_cell (Eqs. 4,
+// 6-17), with the equilibrium evaluated per opposite-link pair
+// (feq_i, feq_opp(i) = common +- odd part).
+
+// Flow collision (Eqs. 6-9, 15-17), Darcy drag (Eq. 4) and heat collision
+// (Eqs. 11-13) of one interior cell, in place: q = 0..8 flow, 9..12 T_1..T_4.
+__device__ __forceinline__ void collide_interior(float* f, bool porous, const Phys<float>& ph) {
+    const float ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const float uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    const float usq = ux * ux + uy * uy;
+    const float S0 = float(K_W0) * (-1.5f * usq);
+    const float sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const float p = (sum18 + S0) * 0.6f;
+    const float Tm = f[9] + f[10] + f[11] + f[12];
+    const float om = ph.omega;
+    // equilibrium per opposite pair: common = kappa p + w (4.5 eu^2 - 1.5 usq), odd = 3 w eu
+    const float c_ax = float(K_LAMBDA) * p - float(1.5 * K_W1) * usq;
+    const float c_dg = float(K_GAMMA) * p - float(1.5 * K_W5) * usq;
+    const float e5 = ux + uy, e6 = uy - ux;
+    const float q1 = c_ax + float(4.5 * K_W1) * ux * ux, o1 = float(3.0 * K_W1) * ux;
+    const float q2 = c_ax + float(4.5 * K_W1) * uy * uy, o2 = float(3.0 * K_W1) * uy;
+    const float q5 = c_dg + float(4.5 * K_W5) * e5 * e5, o5 = float(3.0 * K_W5) * e5;
+    const float q6 = c_dg + float(4.5 * K_W5) * e6 * e6, o6 = float(3.0 * K_W5) * e6;
+    const float feq0 = float(-4.0 * K_SIGMA) * p + S0;
+    // body force F = drive - g beta (T - T0) g_hat; F_i = (1/2) e_i . F on the axis links
+    const float gb = ph.g_beta * (Tm - ph.T0);
+    const float Fx = ph.drive_x - gb * ph.gx;
+    const float Fy = ph.drive_y - gb * ph.gy;
+    const float F1 = 0.5f * Fx, F2 = 0.5f * Fy;
+    f[0] = f[0] - om * (f[0] - feq0);
+    f[1] = f[1] - om * (f[1] - (q1 + o1)) + F1;
+    f[3] = f[3] - om * (f[3] - (q1 - o1)) - F1;
+    f[2] = f[2] - om * (f[2] - (q2 + o2)) + F2;
+    f[4] = f[4] - om * (f[4] - (q2 - o2)) - F2;
+    f[5] = f[5] - om * (f[5] - (q5 + o5));
+    f[7] = f[7] - om * (f[7] - (q5 - o5));
+    f[6] = f[6] - om * (f[6] - (q6 + o6));
+    f[8] = f[8] - om * (f[8] - (q6 - o6));
+    if (porous) {
+        const float umx = (ux + 0.5f * Fx) / ph.den;
+        const float umy = (uy + 0.5f * Fy) / ph.den;
+        const float FDx = -ph.cK * umx, FDy = -ph.cK * umy;
+        const float a1 = float(3.0 * K_W1), a5 = float(3.0 * K_W5);
+        f[1] += a1 * FDx;
+        f[3] -= a1 * FDx;
+        f[2] += a1 * FDy;
+        f[4] -= a1 * FDy;
+        f[5] += a5 * (FDx + FDy);
+        f[7] -= a5 * (FDx + FDy);
+        f[6] += a5 * (FDy - FDx);
+        f[8] -= a5 * (FDy - FDx);
+    }
+    const float omT = ph.omegaT, Tq = 0.25f * Tm;
+    f[9] = f[9] - omT * (f[9] - Tq * (1.0f + 2.0f * ux));
+    f[10] = f[10] - omT * (f[10] - Tq * (1.0f + 2.0f * uy));
+    f[11] = f[11] - omT * (f[11] - Tq * (1.0f - 2.0f * ux));
+    f[12] = f[12] - omT * (f[12] - Tq * (1.0f - 2.0f * uy));
+}
+
+template <class ST, int PAR>
+__device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, int y, bool por0,
+                                                     bool por1) {
+    using T = typename ST::T;
+    const int nx = d.nx, ny = d.ny;
+    const int np = (int)d.npad;
+    T* const P = static_cast<T*>(d.pops);
+    const int lane = threadIdx.x & 31;
+    const int row = y * nx;
+    const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
+    const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
+    const int xl = x == 0 ? nx - 1 : x - 1;     // column left of the pair
+    const int xr = x + 2 == nx ? 0 : x + 2;     // column right of the pair
+    float a[13], b[13];                          // cells x and x+1; 9..12 = T_1..T_4
+
+    // ---- load ---------------------------------------------------------------
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float2 v = ST::ldf2(P + q * np + row + x, d);
+            a[q] = v.x;
+            b[q] = v.y;
+        }
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) {
+            const float2 v = ST::ldT2(P + (8 + i) * np + row + x, d);
+            a[8 + i] = v.x;
+            b[8 + i] = v.y;
+        }
+    } else {
+        {
+            const float2 v = ST::ldf2(P + row + x, d);
+            a[0] = v.x;
+            b[0] = v.y;
+        }
+#pragma unroll
+        for (int k = 1; k < 13; ++k) {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;            // lattice direction
+            const int pl = heat ? 8 + opp(i) : opp(i); // f_i(x) sits in slot (x - e_i, opp(i))
+            const int sr = ey(i) == 1 ? rowd : (ey(i) == -1 ? rowu : row);
+            const T* src = P + pl * np + sr;
+            const float2 v = heat ? ST::ldT2(src + x, d) : ST::ldf2(src + x, d);
+            if (ex(i) == 0) {
+                a[k] = v.x;
+                b[k] = v.y;
+            } else if (ex(i) == 1) {  // source columns x-1, x
+                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
+                if (lane == 0) left = heat ? ST::ldT(src + xl, d) : ST::ldf(src + xl, d);
+                a[k] = left;
+                b[k] = v.x;
+            } else {                  // source columns x+1, x+2
+                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+                if (lane == 31) right = heat ? ST::ldT(src + xr, d) : ST::ldf(src + xr, d);
+                a[k] = v.y;
+                b[k] = right;
+            }
+        }
+    }
+
+    collide_interior(a, por0, d.pf);
+    collide_interior(b, por1, d.pf);
+
+    // ---- store --------------------------------------------------------------
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+    } else {
+        ST::stf2(P + row + x, a[0], b[0], d);
+#pragma unroll
+        for (int k = 1; k < 13; ++k) {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;
+            const int pl = heat ? 8 + i : i;           // f*_i(x) goes to slot (x + e_i, i)
+            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
+            T* dst = P + pl * np + dr;
+            if (ex(i) == 0) {
+                if (heat) ST::stT2(dst + x, a[k], b[k], d);
+                else ST::stf2(dst + x, a[k], b[k], d);
+            } else if (ex(i) == 1) {  // destination columns x+1, x+2
+                const float left = __shfl_up_sync(0xffffffffu, b[k], 1);
+                if (lane != 0) {
+                    if (heat) ST::stT2(dst + x, left, a[k], d);
+                    else ST::stf2(dst + x, left, a[k], d);
+                } else {
+                    if (heat) ST::stT(dst + x + 1, a[k], d);
+                    else ST::stf(dst + x + 1, a[k], d);
+                }
+                if (lane == 31) {
+                    if (heat) ST::stT(dst + xr, b[k], d);
+                    else ST::stf(dst + xr, b[k], d);
+                }
+            } else {                  // destination columns x-1, x
+                const float right = __shfl_down_sync(0xffffffffu, a[k], 1);
+                if (lane != 31) {
+                    if (heat) ST::stT2(dst + x, b[k], right, d);
+                    else ST::stf2(dst + x, b[k], right, d);
+                } else {
+                    if (heat) ST::stT(dst + x, b[k], d);
+                    else ST::stf(dst + x, b[k], d);
+                }
+                if (lane == 0) {
+                    if (heat) ST::stT(dst + xl, a[k], d);
+                    else ST::stf(dst + xl, a[k], d);
+                }
+            }
+        }
+    }
+}
+
+template <class ST, bool OBS, int PAR>
+__device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, int rpt,
+                                          double* acc) {
+    constexpr int V = sizeof(typename ST::R) == 4 ? LBM_PAIR_CELLS : 1;
+    const int x = te.z + V * threadIdx.x;
+    if constexpr (V == 1 && !OBS && sizeof(typename ST::R) == 4) {
+        tile_rows_pipelined<ST, PAR>(sd, te, rpt);
+    } else if constexpr (V == 2) {
+        // the pair path needs whole warps on one row and even rows
+        const bool vec_ok = !OBS && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0;
+        for (int r = 0; r < rpt; ++r) {
+            const int y = te.w + threadIdx.y + r * blockDim.y;
+            bool fast = false;
+            if (vec_ok) {
+                const bool in = y < sd.ny && x + 1 < sd.nx;
+                const uint32_t m2 =
+                    in ? *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x) : 0xFFFFu;
+                // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
+                fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+                if (fast) update_pair_interior<ST, PAR>(sd, x, y, (m2 & 1u) != 0, (m2 & 0x100u) != 0);
+            }
+            if (!fast) {
+                if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);
+                if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x + 1, y, mode, acc);
+            }
+        }
+    } else {
+        for (int r = 0; r < rpt; ++r) {
+            const int y = te.w + threadIdx.y + r * blockDim.y;
+            if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Staged step of the FP32-arithmetic kernels.  A block of NT threads walks a
+// strip of W = 2 NT cells x H rows, one row at a time.  The 13 population
+// segments each row needs (own slots on an even step; on an odd step the
+// source row of each plane, widened by a 16-byte halo on both sides for the
+// x-shifted links) are copied into shared memory with cp.async, STAGES - 1 rows
+// ahead of the row being computed, so the loads of later rows are in flight
+// while a row is computed and no register holds a pending load.  Each thread
+// then updates a cell pair from shared memory (interior pairs with
+// collide_interior, every other active cell with cell_body) and stores to
+// global memory in the AA pattern.  Rows never share a slot (each slot is read
+// and written only by the cell that owns it), so copying later rows before
+// this row's stores land is exact.  Halo elements that belong to cells of a
+// neighbouring strip are copied but never used.
+
+constexpr int STAGES = 3;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// elements per 16-byte chunk, and shared-memory segment length per plane
+template <class T>
+__host__ __device__ constexpr int chunk_elems() { return 16 / (int)sizeof(T); }
+template <class T>
+__host__ __device__ constexpr int seg_elems(int W) { return W + 2 * chunk_elems<T>(); }
+template <class T>
+__host__ __device__ constexpr size_t staged_smem_bytes(int W) {
+    return (size_t)STAGES * 13 * seg_elems<T>(W) * sizeof(T);
+}
+
+// source row of plane p for target row y on an odd step: f_i(x) sits in slot
+// (x - e_i, opp(i)), i.e. plane p = opp(i) holds it at row y - ey(i) = y + ey(p)
+__device__ __forceinline__ constexpr int plane_dir(int p) { return p < 9 ? p : p - 8; }
+
+template <class ST>
+__device__ __forceinline__ void staged_issue(const InstDesc& sd, typename ST::T* stage, int x0, int W,
+                                             int y, int parity) {
+    using T = typename ST::T;
+    constexpr int CHE = chunk_elems<T>();
+    const int SEG = W + 2 * CHE;
+    const int nch = SEG / CHE;
+    const T* P = static_cast<const T*>(sd.pops);
+    const int np = (int)sd.npad;
+    const int total = 13 * nch;
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int p = k / nch, ch = k - p * nch;
+        if (parity == 0 && (ch == 0 || ch == nch - 1)) continue;  // even: no halo needed
+        const int col = x0 - CHE + ch * CHE;
+        if (col < 0 || col + CHE > sd.nx) continue;
+        int row = y;
+        if (parity) {
+            row = y + ey(plane_dir(p));
+            if (row < 0) row += sd.ny;
+            if (row >= sd.ny) row -= sd.ny;
+        }
+        cp_async16(stage + p * SEG + ch * CHE, P + p * np + row * sd.nx + col);
+    }
+}
+
+template <class ST, int PAR>
+__device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST::T* stage, int x0,
+                                           int W, int y) {
+    using T = typename ST::T;
+    using R = float;
+    constexpr int CHE = chunk_elems<T>();
+    const int SEG = W + 2 * CHE;
+    const int nx = sd.nx;
+    const int x = x0 + 2 * (int)threadIdx.x;
+    if (x >= nx) return;
+    const uint32_t m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * nx + x);
+    if ((m2 & 7u) > POROUS && ((m2 >> 8) & 7u) > POROUS) return;  // neither cell is active
+    // the pair's wrap-around columns at a periodic edge are not staged: use
+    // the direct path there
+    if (x == 0 || x + 2 >= nx) {
+        update_cell<ST, false, PAR>(sd, x, y, 0, nullptr);
+        if (x + 1 < nx) update_cell<ST, false, PAR>(sd, x + 1, y, 0, nullptr);
+        return;
+    }
+    const int j = x - x0 + CHE;  // stage column of cell x
+    float a[13], b[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        const bool heat = k > 8;
+        const int i = heat ? k - 8 : k;
+        const int pl = PAR == 0 ? k : (heat ? 8 + opp(i) : opp(i));
+        const int jj = PAR == 0 ? j : j - ex(i);
+        const T* src = stage + pl * SEG + jj;
+        if (heat) {
+            a[k] = ST::ldT(src, sd);
+            b[k] = ST::ldT(src + 1, sd);
+        } else {
+            a[k] = ST::ldf(src, sd);
+            b[k] = ST::ldf(src + 1, sd);
+        }
+    }
+    const bool interior = (m2 & 0x0E0Eu) == 0u;
+    if (!interior) {
+        // at least one cell next to a boundary (or solid): general update of
+        // each active cell with the staged populations
+        for (int v = 0; v < 2; ++v) {
+            const float* c = v == 0 ? a : b;
+            R f[9], g[4];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = c[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g[i] = c[9 + i];
+            cell_body<ST, false, PAR>(sd, x + v, y, f, g, (uint8_t)(m2 >> (8 * v)), 0, nullptr);
+        }
+        return;
+    }
+    collide_interior(a, (m2 & 1u) != 0, sd.pf);
+    collide_interior(b, (m2 & 0x100u) != 0, sd.pf);
+    T* const P = static_cast<T*>(sd.pops);
+    const int np = (int)sd.npad;
+    const int ny = sd.ny;
+    const int row = y * nx;
+    const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
+    const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], sd);
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], sd);
+    } else {
+        ST::stf2(P + row + x, a[0], b[0], sd);
+#pragma unroll
+        for (int k = 1; k < 13; ++k) {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;
+            const int pl = heat ? 8 + i : i;  // f*_i(x) goes to slot (x + e_i, i)
+            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
+            T* dst = P + pl * np + dr + x;
+            if (ex(i) == 0) {
+                if (heat) ST::stT2(dst, a[k], b[k], sd);
+                else ST::stf2(dst, a[k], b[k], sd);
+            } else {
+                const int o = ex(i);
+                if (heat) {
+                    ST::stT(dst + o, a[k], sd);
+                    ST::stT(dst + 1 + o, b[k], sd);
+                } else {
+                    ST::stf(dst + o, a[k], sd);
+                    ST::stf(dst + 1 + o, b[k], sd);
+                }
+            }
+        }
+    }
+}
+
+template <class ST>
+__global__ void __launch_bounds__(128) step_kernel_staged(const InstDesc* __restrict__ insts,
+                                                          const int4* __restrict__ tiles, int ntiles,
+                                                          int flip, int mode, Shape shape) {
+    using T = typename ST::T;
+    extern __shared__ __align__(16) unsigned char staged_smem[];
+    __shared__ __align__(16) InstDesc sd;
+    T* const buf = reinterpret_cast<T*>(staged_smem);
+    const int W = 2 * (int)blockDim.x;
+    const int SEG = seg_elems<T>(W);
+    const int H = shape.rpt;
+    (void)mode;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 te = tiles[t];
+        __syncthreads();
+        {
+            const uint64_t* src = reinterpret_cast<const uint64_t*>(insts + te.x);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&sd);
+            for (int k = threadIdx.x; k < (int)(sizeof(InstDesc) / 8); k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();
+        const int parity = (sd.parity ^ flip) & 1;
+        const int x0 = te.z, y0 = te.w;
+        const int rows = min(H, sd.ny - y0);
+        if ((sd.nx % chunk_elems<T>()) != 0) {
+            // rows not 16-byte aligned: direct loads
+            for (int r = 0; r < rows; ++r) {
+                const int x = x0 + 2 * (int)threadIdx.x;
+                for (int v = 0; v < 2; ++v)
+                    if (x + v < sd.nx) {
+                        if (parity) update_cell<ST, false, 1>(sd, x + v, y0 + r, 0, nullptr);
+                        else update_cell<ST, false, 0>(sd, x + v, y0 + r, 0, nullptr);
+                    }
+            }
+            continue;
+        }
+#pragma unroll
+        for (int r = 0; r < STAGES - 1; ++r) {
+            if (r < rows) staged_issue<ST>(sd, buf + (r % STAGES) * 13 * SEG, x0, W, y0 + r, parity);
+            cp_async_commit();
+        }
+        for (int r = 0; r < rows; ++r) {
+            const int rn = r + STAGES - 1;
+            if (rn < rows) staged_issue<ST>(sd, buf + (rn % STAGES) * 13 * SEG, x0, W, y0 + rn, parity);
+            cp_async_commit();
+            cp_async_wait<STAGES - 1>();
+            __syncthreads();
+            const T* stage = buf + (r % STAGES) * 13 * SEG;
+            if (parity) staged_row<ST, 1>(sd, stage, x0, W, y0 + r);
+            else staged_row<ST, 0>(sd, stage, x0, W, y0 + r);
+            __syncthreads();
+        }
+        cp_async_wait<0>();
+    }
+}
+
 template <class ST, bool OBS>
-__global__ void __launch_bounds__(256, (OBS || sizeof(typename ST::R) == 8) ? 2 : (sizeof(typename ST::T) == 2 ? 3 : 4)) step_kernel(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
@@ -370,14 +864,8 @@ __global__ void __launch_bounds__(256, (OBS || sizeof(typename ST::R) == 8) ? 2 
         double acc[NPART];
 #pragma unroll
         for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
-        const int x = te.z + threadIdx.x;
-        for (int r = 0; r < shape.rpt; ++r) {
-            const int y = te.w + threadIdx.y + r * blockDim.y;
-            if (x < sd.nx && y < sd.ny) {
-                if (parity) update_cell<ST, OBS, 1>(sd, x, y, mode, acc);
-                else update_cell<ST, OBS, 0>(sd, x, y, mode, acc);
-            }
-        }
+        if (parity) tile_rows<ST, OBS, 1>(sd, te, mode, shape.rpt, acc);
+        else tile_rows<ST, OBS, 0>(sd, te, mode, shape.rpt, acc);
         if (OBS && (mode & OBS_STATS)) {
             warp_block_reduce<double>(acc, red, sd.partials + (int64_t)te.y * NPART);
         }

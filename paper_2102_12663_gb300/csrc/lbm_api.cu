@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "kernel_body.cuh"
 #include "lbm_internal.cuh"
 
@@ -20,10 +20,16 @@ bool build_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info* inf
                 std::string& err);
 void mark_near_boundary(uint8_t* m, int nx, int ny);
 
+StepPlan step_plan(int precision, bool obs, Shape shape) {
+    return precision == 0 ? step_plan_f64(obs, shape) : step_plan_lp(precision, obs, shape);
+}
+
 cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
                         int flip, int mode, Shape shape, int grid, cudaStream_t s) {
-    if (precision == 0) return launch_step_f64(insts, tiles, ntiles, flip, mode, shape, grid, s);
-    return launch_step_lp(precision, insts, tiles, ntiles, flip, mode, shape, grid, s);
+    if (ntiles <= 0) return cudaSuccess;
+    const StepPlan pl = step_plan(precision, mode != 0, shape);
+    void* args[] = {&insts, &tiles, &ntiles, &flip, &mode, &shape};
+    return cudaLaunchKernel(pl.func, dim3(grid), pl.block, args, pl.smem, s);
 }
 }  // namespace lbm
 
@@ -576,10 +582,6 @@ static lbm_status step_once(lbm_domain* d, int mode) {
     return LBM_OK;
 }
 
-static const void* step_fn(int prec, bool obs) {
-    return prec == LBM_F64 ? step_kernel_ptr_f64(obs) : step_kernel_ptr_lp(prec, obs);
-}
-
 // Builds (once per launch shape) a graph of GRAPH_STEPS chained plain steps
 // with alternating parity, replayed by lbm_step from an even step.
 static lbm_status ensure_graph(lbm_domain* d) {
@@ -596,10 +598,12 @@ static lbm_status ensure_graph(lbm_domain* d) {
         int a2 = d->ntiles, a3 = k & 1, a4 = 0;
         Shape a5 = sh;
         void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+        const StepPlan pl = step_plan(d->prec, false, sh);
         cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void*>(step_fn(d->prec, false));
+        kp.func = const_cast<void*>(pl.func);
         kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(sh.tw, sh.bh);
+        kp.blockDim = pl.block;
+        kp.sharedMemBytes = (unsigned)pl.smem;
         kp.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
@@ -1017,10 +1021,12 @@ static lbm_status batch_ensure_graph(lbm_batch* b) {
         int a2 = b->ntiles, a3 = k & 1, a4 = 0;
         Shape a5 = sh;
         void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+        const StepPlan pl = step_plan(b->prec, false, sh);
         cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void*>(step_fn(b->prec, false));
+        kp.func = const_cast<void*>(pl.func);
         kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(sh.tw, sh.bh);
+        kp.blockDim = pl.block;
+        kp.sharedMemBytes = (unsigned)pl.smem;
         kp.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);

@@ -84,8 +84,19 @@ template <>
 __host__ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDesc& d) { return d.pf; }
 
 struct Shape {
-    int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = tw x bh threads
+    int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = (tw / V) x bh threads
 };
+
+// Cells per thread along x of the FP32-arithmetic kernels: 2 selects the
+// cell-pair path (vector loads and stores, warp shuffles), 1 the
+// software-pipelined one-cell-per-thread path.  The FP64 kernel always takes
+// single cells.
+#ifndef LBM_PAIR_CELLS
+#define LBM_PAIR_CELLS 2
+#endif
+__host__ __device__ constexpr int cells_per_thread(int precision) {
+    return precision == 0 ? 1 : LBM_PAIR_CELLS;
+}
 
 // ---- storage traits --------------------------------------------------------
 struct StF64 {
@@ -103,6 +114,15 @@ struct StF32 {
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { *p = v; }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
+    // two neighbouring cells (p 8-byte aligned)
+    static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc&) {
+        return *reinterpret_cast<const float2*>(p);
+    }
+    static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc&) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+    static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) { return ldf2(p, d); }
+    static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) { stf2(p, a, b, d); }
 };
 struct StF16 {
     using T = __half;
@@ -118,6 +138,21 @@ struct StF16 {
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
         *p = __float2half_rn((v - d.Tshift) * d.fscale);
+    }
+    static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        return make_float2(v.x * d.finv, v.y * d.finv);
+    }
+    static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * d.fscale, b * d.fscale);
+    }
+    static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
+    }
+    static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
+        *reinterpret_cast<__half2*>(p) =
+            __floats2half2_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale);
     }
 };
 struct StBF16 {
@@ -135,19 +170,38 @@ struct StBF16 {
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
         *p = __float2bfloat16_rn((v - d.Tshift) * d.fscale);
     }
+    static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        return make_float2(v.x * d.finv, v.y * d.finv);
+    }
+    static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a * d.fscale, b * d.fscale);
+    }
+    static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
+    }
+    static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
+        *reinterpret_cast<__nv_bfloat162*>(p) =
+            __floats2bfloat162_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale);
+    }
 };
 
 // ---- launchers (one translation unit per arithmetic precision) -----------
 // precision: 0 f64, 1 f32, 2 f16-dev, 3 bf16-dev.
 cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
                         int flip, int mode, Shape shape, int grid, cudaStream_t s);
-cudaError_t launch_step_f64(const InstDesc* insts, const int4* tiles, int ntiles, int flip,
-                            int mode, Shape shape, int grid, cudaStream_t s);
-cudaError_t launch_step_lp(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
-                           int flip, int mode, Shape shape, int grid, cudaStream_t s);
 cudaError_t launch_finalize(const InstDesc* insts, int ninst, cudaStream_t s);
-// device entry of the step kernel (for CUDA graph kernel nodes)
-const void* step_kernel_ptr_f64(bool obs);
-const void* step_kernel_ptr_lp(int precision, bool obs);
+
+// Kernel, block shape and dynamic shared memory of one step launch (also the
+// parameters of a CUDA graph kernel node).
+struct StepPlan {
+    const void* func;
+    dim3 block;
+    size_t smem;
+};
+StepPlan step_plan(int precision, bool obs, Shape shape);
+StepPlan step_plan_f64(bool obs, Shape shape);
+StepPlan step_plan_lp(int precision, bool obs, Shape shape);
 
 }  // namespace lbm

@@ -19,7 +19,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "kernel_body.cuh"
 
 namespace lbm {

@@ -5,18 +5,13 @@
 
 namespace lbm {
 
-cudaError_t launch_step_f64(const InstDesc* insts, const int4* tiles, int ntiles, int flip,
-                            int mode, Shape shape, int grid, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
-    dim3 block(shape.tw, shape.bh);
-    if (mode == 0) step_kernel<StF64, false><<<grid, block, 0, s>>>(insts, tiles, ntiles, flip, 0, shape);
-    else step_kernel<StF64, true><<<grid, block, 0, s>>>(insts, tiles, ntiles, flip, mode, shape);
-    return cudaGetLastError();
-}
-
-const void* step_kernel_ptr_f64(bool obs) {
-    return obs ? reinterpret_cast<const void*>(&step_kernel<StF64, true>)
-               : reinterpret_cast<const void*>(&step_kernel<StF64, false>);
+StepPlan step_plan_f64(bool obs, Shape shape) {
+    StepPlan p;
+    p.func = obs ? reinterpret_cast<const void*>(&step_kernel<StF64, true>)
+                 : reinterpret_cast<const void*>(&step_kernel<StF64, false>);
+    p.block = dim3(shape.tw, shape.bh);
+    p.smem = 0;
+    return p;
 }
 
 }  // namespace lbm

@@ -1,35 +1,32 @@
 // FP32-arithmetic instantiations of the fused step: FP32 storage and the two
-// 16-bit deviation storages (FP16 scaled, BF16).
+// 16-bit deviation storages (FP16 scaled, BF16).  Plain steps with one row of
+// threads per block take the cp.async-staged kernel; observing steps and
+// other shapes take the direct kernel.
 #include "kernel_body.cuh"
 
 namespace lbm {
 
 template <class ST>
-static cudaError_t launch_t(const InstDesc* insts, const int4* tiles, int ntiles, int flip, int mode,
-                            Shape shape, int grid, cudaStream_t s) {
-    dim3 block(shape.tw, shape.bh);
-    if (mode == 0) step_kernel<ST, false><<<grid, block, 0, s>>>(insts, tiles, ntiles, flip, 0, shape);
-    else step_kernel<ST, true><<<grid, block, 0, s>>>(insts, tiles, ntiles, flip, mode, shape);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step_lp(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
-                           int flip, int mode, Shape shape, int grid, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
-    switch (precision) {
-    case 1: return launch_t<StF32>(insts, tiles, ntiles, flip, mode, shape, grid, s);
-    case 2: return launch_t<StF16>(insts, tiles, ntiles, flip, mode, shape, grid, s);
-    case 3: return launch_t<StBF16>(insts, tiles, ntiles, flip, mode, shape, grid, s);
-    default: return cudaErrorInvalidValue;
+static StepPlan plan_t(bool obs, Shape shape) {
+    StepPlan p;
+    if (!obs && shape.bh == 1) {
+        p.func = reinterpret_cast<const void*>(&step_kernel_staged<ST>);
+        p.block = dim3(shape.tw / 2, 1);
+        p.smem = staged_smem_bytes<typename ST::T>(shape.tw);
+    } else {
+        p.func = obs ? reinterpret_cast<const void*>(&step_kernel<ST, true>)
+                     : reinterpret_cast<const void*>(&step_kernel<ST, false>);
+        p.block = dim3(shape.tw / cells_per_thread(1), shape.bh);
+        p.smem = 0;
     }
+    return p;
 }
 
-const void* step_kernel_ptr_lp(int precision, bool obs) {
+StepPlan step_plan_lp(int precision, bool obs, Shape shape) {
     switch (precision) {
-    case 1: return obs ? (const void*)&step_kernel<StF32, true> : (const void*)&step_kernel<StF32, false>;
-    case 2: return obs ? (const void*)&step_kernel<StF16, true> : (const void*)&step_kernel<StF16, false>;
-    case 3: return obs ? (const void*)&step_kernel<StBF16, true> : (const void*)&step_kernel<StBF16, false>;
-    default: return nullptr;
+    case 1: return plan_t<StF32>(obs, shape);
+    case 2: return plan_t<StF16>(obs, shape);
+    default: return plan_t<StBF16>(obs, shape);
     }
 }
 

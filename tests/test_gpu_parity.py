@@ -146,6 +146,25 @@ def test_periodic_channel_and_porous_box():
     assert rel_err(dom, ref) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("launch", [
+    dict(tile_w=64, block_rows=1, rows_per_thread=16, blocks_per_sm=0),
+    dict(tile_w=128, block_rows=1, rows_per_thread=5, blocks_per_sm=1),
+])
+def test_periodic_wrap_low_precision(prec, launch):
+    """Wrap-around columns and rows on the FP32-arithmetic paths (pairs at a
+    periodic edge, strips that wrap in y), against the FP64 oracle."""
+    m, d = W.porous_box(64, 24)
+    m[5:9, 20:30] = 1
+    m[12:14, :] = 0  # a fluid lane across the periodic box
+    P = dict(tau=0.7, tau_T=0.8, drive=(1e-5, -3e-6), K_tm=0.2, noise_amp=1e-3, T0=0.3,
+             g_beta=1e-4, g_dir=(0.6, -0.8), seed=9)
+    dom, ref = mask_pair(m, d, prec, P, launch=launch)
+    dom.step(60)
+    ref.run(60)
+    assert rel_err(dom, ref) <= (tol("f32", 60) if prec == "f32" else 3e-3)
+
+
 def test_darcy_column_plug_inlet_outlet():
     m, d = W.darcy_column(8, 32, 8, 6)
     P = dict(tau=0.8, u_in_max=1e-4, K_tm=0.5, T_in=1.0, T0=0.5)
