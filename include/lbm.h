@@ -107,6 +107,9 @@ typedef struct lbm_geometry_info {
     int64_t n_cells, n_active, n_fluid, n_porous, n_inlet, n_outlet;
     int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
     int32_t eye_normals;     /* 1: analytic cornea / iris wall normals */
+    int32_t outlet_axis;     /* outlets drain along x (0) or y (1): EYE 0, MASK the
+                                inflow axis */
+    int32_t reserved;
     double arc_xc, arc_yc;   /* centre of the cornea arc (EYE) */
 } lbm_geometry_info;
 
@@ -124,7 +127,15 @@ typedef struct lbm_geometry_info {
  *  drive        uniform body force (test flows; 0 for the eye).
  *  noise_amp, seed  amplitude and seed of the initial temperature noise.
  *  dx_m, dt_s, rho0, p_sc_pa  unit conversion for the *_pa outputs:
- *               IOP_pa = p_sc_pa + rho0 (dx/dt)^2 (iop - p_out). */
+ *               IOP_pa = p_sc_pa + rho0 (dx/dt)^2 (iop - p_out).
+ *  tm_model     0: the trabecular meshwork is resolved as porous cells with
+ *               Darcy drag (Eq. 4) and the outlets hold p_out;
+ *               1: the paper's lumped meshwork (Sec. 2.3): no drag in the TM
+ *               cells, and the outlets impose the seepage velocity
+ *               u_s = K_tm (IOP - p_out) / (nu h_tm) (Darcy's law across a
+ *               meshwork of thickness h_tm with a linear pressure profile),
+ *               re-evaluated from the IOP after every steady-state check.
+ *  h_tm         effective meshwork thickness in cells (tm_model 1; > 0). */
 typedef struct lbm_params {
     double tau, tau_T;
     double g_beta;
@@ -137,6 +148,9 @@ typedef struct lbm_params {
     double noise_amp;
     uint64_t seed;
     double dx_m, dt_s, rho0, p_sc_pa;
+    int32_t tm_model;
+    int32_t reserved;
+    double h_tm;
 } lbm_params;
 
 /* Observables of the state at time `step` (pre-collision populations).
@@ -153,6 +167,8 @@ typedef struct lbm_observables {
     int64_t n_fluid, n_cornea, n_iris;
     int32_t nan_flag;             /* non-zero if any pressure was NaN */
     int32_t reserved;
+    double u_seep;                /* seepage speed at the outlets during the
+                                     observed step (tm_model 1, else 0) */
 } lbm_observables;
 
 /* Launch shape of the fused step kernel: tiles of tile_w x (block_rows *

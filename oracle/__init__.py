@@ -41,7 +41,7 @@ class Geom(ctypes.Structure):
         ("inlet_dir_x", ctypes.c_int32), ("inlet_dir_y", ctypes.c_int32),
         ("inlet_profile", ctypes.c_int32),
         ("inlet_lo", ctypes.c_int32), ("inlet_width", ctypes.c_int32),
-        ("eye_normals", ctypes.c_int32),
+        ("eye_normals", ctypes.c_int32), ("outlet_axis", ctypes.c_int32),
         ("arc_xc", ctypes.c_double), ("arc_yc", ctypes.c_double),
     ]
 
@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("u_in_max", ctypes.c_double), ("K", ctypes.c_double),
         ("p_out", ctypes.c_double), ("drive", ctypes.c_double * 2),
         ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("tm_model", ctypes.c_int32), ("pad0", ctypes.c_int32), ("u_seep", ctypes.c_double),
     ]
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.orc_fields.argtypes = [ctypes.POINTER(Geom), u8p, dp, dp, dp, dp, dp]
         L.orc_run.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Params), u8p,
                               dp, dp, dp, dp, ctypes.c_int64]
+        L.orc_seepage_velocity.restype = ctypes.c_double
+        L.orc_seepage_velocity.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double]
         L.orc_set_threads.argtypes = [ctypes.c_int32]
         L.orc_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -147,6 +150,8 @@ def make_params(**kw) -> Params:
     P.drive[0], P.drive[1] = float(dr[0]), float(dr[1])
     P.noise_amp = kw.get("noise_amp", 0.0)
     P.seed = int(kw.get("seed", 0)) & (2**64 - 1)
+    P.tm_model = int(kw.get("tm_model", 0))
+    P.u_seep = float(kw.get("u_seep", 0.0))
     return P
 
 
@@ -164,8 +169,9 @@ def eye_mask(nx: int, ny: int, angle_deg: float = 45.0, band: int = 0,
 
 def mask_geom(nx: int, ny: int, periodic_x: int = 0, periodic_y: int = 0,
               inlet_dir=(0, 1), inlet_profile: int = 0, inlet_lo: int = 0,
-              inlet_width: int = 1) -> Geom:
+              inlet_width: int = 1, outlet_axis: int | None = None) -> Geom:
     g = Geom()
+    g.outlet_axis = (0 if inlet_dir[0] != 0 else 1) if outlet_axis is None else outlet_axis
     g.nx, g.ny = nx, ny
     g.periodic_x, g.periodic_y = periodic_x, periodic_y
     g.inlet_dir_x, g.inlet_dir_y = int(inlet_dir[0]), int(inlet_dir[1])
@@ -173,6 +179,11 @@ def mask_geom(nx: int, ny: int, periodic_x: int = 0, periodic_y: int = 0,
     g.inlet_lo, g.inlet_width = inlet_lo, inlet_width
     g.eye_normals = 0
     return g
+
+
+def seepage_velocity(params: Params, iop: float, h_tm: float) -> float:
+    """Lumped TM (Sec. 2.3): seepage speed for the current IOP."""
+    return float(lib().orc_seepage_velocity(ctypes.byref(params), float(iop), float(h_tm)))
 
 
 def feq(p: float, ux: float, uy: float) -> np.ndarray:

@@ -139,6 +139,7 @@ int orc_eye_mask(int32_t nx, int32_t ny, double angle_deg, int32_t band,
     geom->inlet_lo = xin0;
     geom->inlet_width = inlet_w;
     geom->eye_normals = 1;
+    geom->outlet_axis = 0;
     geom->arc_xc = xc;
     geom->arc_yc = yc;
     return 0;
@@ -274,7 +275,8 @@ void orc_step(const orc_geom* G, const orc_params* P, const uint8_t* type,
             orc_moments(fc, &p, &ux, &uy);
             double usq = ux * ux + uy * uy;
             double Tm = temperature(gc);
-            orc_collide(P, type[c] == ORC_POROUS, fc, gc, fs, gs);
+            /* the lumped TM of Sec. 2.3 resolves no Darcy flow inside the TM block */
+            orc_collide(P, type[c] == ORC_POROUS && P->tm_model == 0, fc, gc, fs, gs);
             fn[c] = fs[0];
             for (int i = 1; i < 9; ++i) {
                 int64_t nb = neighbour(G, x, y, i);
@@ -288,6 +290,14 @@ void orc_step(const orc_geom* G, const orc_params* P, const uint8_t* type,
                     double v = fs[i] - 6.0 * W[i] * (EX[i] * uix + EY[i] * uiy);
                     fn[o * N + c] = v;
                     q_in += v - fs[i];
+                } else if (tn == ORC_OUTLET && P->tm_model == 1) {
+                    /* lumped TM (Sec. 2.3): the seepage velocity, directed out
+                     * of the domain along the outlet axis, as a moving wall */
+                    double uwx = G->outlet_axis == 0 ? P->u_seep * EX[i] : 0.0;
+                    double uwy = G->outlet_axis == 1 ? P->u_seep * EY[i] : 0.0;
+                    double v = fs[i] - 6.0 * W[i] * (EX[i] * uwx + EY[i] * uwy);
+                    fn[o * N + c] = v;
+                    q_out += fs[i] - v;
                 } else if (tn == ORC_OUTLET) {
                     double eu = EX[i] * ux + EY[i] * uy;
                     double kappa = i <= 4 ? LAMBDA : GAMMA;
@@ -446,6 +456,15 @@ void orc_observe(const orc_geom* G, const orc_params* P, const uint8_t* type,
     o->n_fluid = n_fluid;
     o->n_cornea = nc;
     o->n_iris = ni;
+}
+
+/* Lumped TM of Sec. 2.3: Darcy's law (Eq. 4) across a meshwork of thickness
+ * h_tm with a linear pressure profile, u_s = (K/mu) (p_IOP - p_0) / h_tm, in
+ * kinematic lattice units u_s = K (iop - p_out) / (nu h_tm), nu from Eq. 10. */
+double orc_seepage_velocity(const orc_params* P, double iop, double h_tm)
+{
+    double nu = (2.0 * P->tau - 1.0) / 6.0;
+    return P->K * (iop - P->p_out) / (nu * h_tm);
 }
 
 void orc_fields(const orc_geom* G, const uint8_t* type, const double* f,

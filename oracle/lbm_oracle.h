@@ -28,6 +28,7 @@ typedef struct {
     int32_t inlet_lo, inlet_width;    /* gap start and width, measured along the
                                          axis perpendicular to the inflow */
     int32_t eye_normals;              /* 1: analytic eye wall normals */
+    int32_t outlet_axis;              /* 0: outlets drain along x, 1: along y */
     double arc_xc, arc_yc;            /* centre of the cornea arc (eye only) */
 } orc_geom;
 
@@ -44,6 +45,10 @@ typedef struct {
     double drive[2];       /* uniform body force (test flows) */
     double noise_amp;      /* amplitude of the seeded temperature noise */
     uint64_t seed;
+    int32_t tm_model;      /* 0: porous TM cells with Darcy drag; 1: the lumped
+                              TM of Sec. 2.3 (seepage-velocity outflow) */
+    int32_t pad0;
+    double u_seep;         /* lumped TM: current seepage speed out of the outlets */
 } orc_params;
 
 typedef struct {
@@ -72,6 +77,7 @@ void orc_step(const orc_geom* G, const orc_params* P, const uint8_t* type,
 void orc_observe(const orc_geom* G, const orc_params* P, const uint8_t* type,
                  const double* f, const double* T, const double* u_snap,
                  orc_obs* obs);
+double orc_seepage_velocity(const orc_params* P, double iop, double h_tm);
 void orc_fields(const orc_geom* G, const uint8_t* type, const double* f,
                 const double* T, double* u, double* p, double* Tf);
 void orc_run(const orc_geom* G, const orc_params* P, const uint8_t* type,

@@ -86,6 +86,7 @@ static bool eye_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info
         info->inlet_lo = gap0;
         info->inlet_width = w_in;
         info->eye_normals = 1;
+        info->outlet_axis = 0;
         info->arc_xc = x_mid;
         info->arc_yc = y_ctr;
     }
@@ -122,6 +123,7 @@ bool build_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info* inf
         tmp.inlet_lo = g.inlet_lo;
         tmp.inlet_width = g.inlet_width;
         tmp.eye_normals = 0;
+        tmp.outlet_axis = g.inlet_dir_x != 0 ? 0 : 1;
     } else {
         err = "unknown geometry kind";
         return false;

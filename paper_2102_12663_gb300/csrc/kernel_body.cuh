@@ -278,7 +278,8 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     fs[4] = fs[4] + (-F2);
 
     // ---- Darcy drag in porous cells, Eq. 4 at the mid-step velocity ---------
-    if (type == POROUS) {
+    // (the lumped meshwork of Sec. 2.3 resolves no flow resistance in the TM)
+    if (type == POROUS && d.tm_model == 0) {
         const R den = ph.den, cK = ph.cK;
         const R umx = (ux + R(0.5) * Fx) / den;
         const R umy = (uy + R(0.5) * Fy) / den;
@@ -331,6 +332,13 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                 const R uix = uin * R(d.inlet_dir_x), uiy = uin * R(d.inlet_dir_y);
                 v = fs[i] - R(6.0 * wgt(i)) * (R(ex(i)) * uix + R(ey(i)) * uiy);
                 if (OBS) q_in += (double)(v - fs[i]);
+            } else if (tn == OUTLET && d.tm_model == 1) {
+                // lumped TM (Sec. 2.3): the seepage velocity, out of the domain
+                // along the outlet axis, as a moving wall
+                const R uwx = d.outlet_axis == 0 ? ph.u_seep * R(ex(i)) : R(0);
+                const R uwy = d.outlet_axis == 1 ? ph.u_seep * R(ey(i)) : R(0);
+                v = fs[i] - R(6.0 * wgt(i)) * (R(ex(i)) * uwx + R(ey(i)) * uwy);
+                if (OBS) q_out += (double)(fs[i] - v);
             } else if (tn == OUTLET) {
                 // pressure anti-bounce-back: minus f* plus the even part of feq(p_out, u)
                 const R kap = i <= 4 ? R(K_LAMBDA) : R(K_GAMMA);
@@ -379,46 +387,6 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
     uint8_t m;
     load_cell<ST, PAR>(d, nb, f, g, m);
     cell_body<ST, OBS, PAR>(d, x, y, f, g, m, mode, acc);
-}
-
-// Rows of a tile with one cell per thread, software-pipelined: the loads of
-// the thread's next row are issued before the current row is computed, so
-// every thread keeps a cell's worth of loads in flight while it computes.
-// Rows never share a slot (each slot is read and written only by the cell
-// that owns it), so reading the next row before storing this one is exact.
-template <class ST, int PAR>
-__device__ __forceinline__ void tile_rows_pipelined(const InstDesc& sd, const int4& te, int rpt) {
-    using R = typename ST::R;
-    const int x = te.z + threadIdx.x;
-    const bool xin = x < sd.nx;
-    int y = te.w + threadIdx.y;
-    bool ok = xin && y < sd.ny;
-    R f[9], g[4];
-    uint8_t m = ADIABATIC;
-    if (ok) {
-        int nb[9];
-        neighbours(sd, x, y, nb);
-        load_cell<ST, PAR>(sd, nb, f, g, m);
-    }
-    for (int r = 0; r < rpt; ++r) {
-        const int yn = y + blockDim.y;
-        const bool ok2 = r + 1 < rpt && xin && yn < sd.ny;
-        R f2[9], g2[4];
-        uint8_t m2 = ADIABATIC;
-        if (ok2) {
-            int nb[9];
-            neighbours(sd, x, yn, nb);
-            load_cell<ST, PAR>(sd, nb, f2, g2, m2);
-        }
-        if (ok) cell_body<ST, false, PAR>(sd, x, y, f, g, m, 0, nullptr);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = f2[i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) g[i] = g2[i];
-        m = m2;
-        y = yn;
-        ok = ok2;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -602,11 +570,9 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
 template <class ST, bool OBS, int PAR>
 __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, int rpt,
                                           double* acc) {
-    constexpr int V = sizeof(typename ST::R) == 4 ? LBM_PAIR_CELLS : 1;
+    constexpr int V = sizeof(typename ST::R) == 4 ? 2 : 1;
     const int x = te.z + V * threadIdx.x;
-    if constexpr (V == 1 && !OBS && sizeof(typename ST::R) == 4) {
-        tile_rows_pipelined<ST, PAR>(sd, te, rpt);
-    } else if constexpr (V == 2) {
+    if constexpr (V == 2) {
         // the pair path needs whole warps on one row and even rows
         const bool vec_ok = !OBS && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0;
         for (int r = 0; r < rpt; ++r) {
@@ -618,7 +584,9 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
                     in ? *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x) : 0xFFFFu;
                 // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
                 fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
-                if (fast) update_pair_interior<ST, PAR>(sd, x, y, (m2 & 1u) != 0, (m2 & 0x100u) != 0);
+                if (fast)
+                    update_pair_interior<ST, PAR>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
+                                                  (m2 & 0x100u) != 0 && sd.tm_model == 0);
             }
             if (!fast) {
                 if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);
@@ -634,68 +602,30 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
 }
 
 // ---------------------------------------------------------------------------
-// Staged step of the FP32-arithmetic kernels.  A block of NT threads walks a
-// strip of W = 2 NT cells x H rows, one row at a time.  The 13 population
-// segments each row needs (own slots on an even step; on an odd step the
-// source row of each plane, widened by a 16-byte halo on both sides for the
-// x-shifted links) are copied into shared memory with cp.async, STAGES - 1 rows
-// ahead of the row being computed, so the loads of later rows are in flight
-// while a row is computed and no register holds a pending load.  Each thread
-// then updates a cell pair from shared memory (interior pairs with
-// collide_interior, every other active cell with cell_body) and stores to
-// global memory in the AA pattern.  Rows never share a slot (each slot is read
-// and written only by the cell that owns it), so copying later rows before
-// this row's stores land is exact.  Halo elements that belong to cells of a
-// neighbouring strip are copied but never used.
-
-constexpr int STAGES = 3;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// Staged step of the FP32-arithmetic kernels (selected by launch shapes with
+// one row of threads per block).  A block of NT threads walks a strip of
+// W = 2 NT cells x H rows, one row at a time.  The 13 population segments each
+// row needs (own slots on an even step; on an odd step the source row of each
+// plane, widened by a 16-byte halo on both sides for the x-shifted links) are
+// copied into shared memory by bulk copies, several rows ahead of the row being
+// computed, so no register holds a pending load.  Each thread then updates a
+// cell pair from shared memory (interior pairs with collide_interior, every
+// other active cell with cell_body) and stores to global memory in the AA
+// pattern.  Rows never share a slot (each slot is read and written only by the
+// cell that owns it), so staging later rows before this row's stores land is
+// exact.  Halo elements that belong to cells of a neighbouring strip are copied
+// but never used.  Measured slower than the direct kernel on the eye
+// workloads; kept as an autotuner candidate.
 
 // elements per 16-byte chunk, and shared-memory segment length per plane
 template <class T>
 __host__ __device__ constexpr int chunk_elems() { return 16 / (int)sizeof(T); }
 template <class T>
 __host__ __device__ constexpr int seg_elems(int W) { return W + 2 * chunk_elems<T>(); }
-template <class T>
-__host__ __device__ constexpr size_t staged_smem_bytes(int W) {
-    return (size_t)STAGES * 13 * seg_elems<T>(W) * sizeof(T);
-}
 
 // source row of plane p for target row y on an odd step: f_i(x) sits in slot
 // (x - e_i, opp(i)), i.e. plane p = opp(i) holds it at row y - ey(i) = y + ey(p)
 __device__ __forceinline__ constexpr int plane_dir(int p) { return p < 9 ? p : p - 8; }
-
-template <class ST>
-__device__ __forceinline__ void staged_issue(const InstDesc& sd, typename ST::T* stage, int x0, int W,
-                                             int y, int parity) {
-    using T = typename ST::T;
-    constexpr int CHE = chunk_elems<T>();
-    const int SEG = W + 2 * CHE;
-    const int nch = SEG / CHE;
-    const T* P = static_cast<const T*>(sd.pops);
-    const int np = (int)sd.npad;
-    const int total = 13 * nch;
-    for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int p = k / nch, ch = k - p * nch;
-        if (parity == 0 && (ch == 0 || ch == nch - 1)) continue;  // even: no halo needed
-        const int col = x0 - CHE + ch * CHE;
-        if (col < 0 || col + CHE > sd.nx) continue;
-        int row = y;
-        if (parity) {
-            row = y + ey(plane_dir(p));
-            if (row < 0) row += sd.ny;
-            if (row >= sd.ny) row -= sd.ny;
-        }
-        cp_async16(stage + p * SEG + ch * CHE, P + p * np + row * sd.nx + col);
-    }
-}
 
 template <class ST, int PAR>
 __device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST::T* stage, int x0,
@@ -748,8 +678,8 @@ __device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST
         }
         return;
     }
-    collide_interior(a, (m2 & 1u) != 0, sd.pf);
-    collide_interior(b, (m2 & 0x100u) != 0, sd.pf);
+    collide_interior(a, (m2 & 1u) != 0 && sd.tm_model == 0, sd.pf);
+    collide_interior(b, (m2 & 0x100u) != 0 && sd.tm_model == 0, sd.pf);
     T* const P = static_cast<T*>(sd.pops);
     const int np = (int)sd.npad;
     const int ny = sd.ny;
@@ -787,18 +717,102 @@ __device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST
     }
 }
 
+// One thread issues the 13 row segments of a row as bulk copies
+// (cp.async.bulk) that complete on the row's shared-memory barrier; TSTAGES
+// rows are in flight per block.  Every wait on a barrier is
+// bounded: if a copy has not landed after TMA_WAIT_LIMIT polls the block sets
+// the device status word, waits (again bounded) for the copies it issued and
+// leaves, and the host reports the error instead of hanging.
+
+constexpr int TSTAGES = 4;
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
+
+// Non-zero after a staged copy failed to complete; read and cleared by the host
+// (take_step_status).  Only the FP32-arithmetic unit instantiates the staged
+// kernels, so its copy of this word is the one that is used.
+static __device__ int g_step_status = 0;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < TMA_WAIT_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Issue row y of a strip (global row sequence g) into stage g % TSTAGES.
+// Every copy starts on a 16-byte boundary and moves a multiple of 16 bytes:
+// x0 and W are multiples of the 16-byte chunk, so are nx (checked) and the
+// plane stride.
 template <class ST>
-__global__ void __launch_bounds__(128) step_kernel_staged(const InstDesc* __restrict__ insts,
-                                                          const int4* __restrict__ tiles, int ntiles,
-                                                          int flip, int mode, Shape shape) {
+__device__ __forceinline__ void tma_issue(const InstDesc& sd, typename ST::T* buf, uint64_t* bars,
+                                          uint32_t g, int x0, int W, int y, int parity) {
     using T = typename ST::T;
-    extern __shared__ __align__(16) unsigned char staged_smem[];
+    constexpr int CHE = chunk_elems<T>();
+    const int SEG = W + 2 * CHE;
+    const int s = (int)(g % TSTAGES);
+    T* stage = buf + (size_t)s * 13 * SEG;
+    const int lo = parity ? max(x0 - CHE, 0) : x0;
+    const int hi = parity ? min(x0 + W + CHE, sd.nx) : min(x0 + W, sd.nx);
+    const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)sizeof(T);
+    const T* P = static_cast<const T*>(sd.pops);
+    const int np = (int)sd.npad;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&bars[s], 13u * bytes);
+    for (int p = 0; p < 13; ++p) {
+        int row = y;
+        if (parity) {
+            row = y + ey(plane_dir(p));
+            if (row < 0) row += sd.ny;
+            if (row >= sd.ny) row -= sd.ny;
+        }
+        bulk_load(stage + p * SEG + (lo - (x0 - CHE)), P + p * np + row * sd.nx + lo, bytes, &bars[s]);
+    }
+}
+
+template <class ST>
+__global__ void __launch_bounds__(128) step_kernel_tma(const InstDesc* __restrict__ insts,
+                                                       const int4* __restrict__ tiles, int ntiles,
+                                                       int flip, int mode, Shape shape) {
+    using T = typename ST::T;
+    extern __shared__ __align__(128) unsigned char tma_smem[];
     __shared__ __align__(16) InstDesc sd;
-    T* const buf = reinterpret_cast<T*>(staged_smem);
+    __shared__ __align__(8) uint64_t bars[TSTAGES];
+    T* const buf = reinterpret_cast<T*>(tma_smem);
     const int W = 2 * (int)blockDim.x;
     const int SEG = seg_elems<T>(W);
     const int H = shape.rpt;
     (void)mode;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < TSTAGES; ++k) mbar_init(&bars[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t seq = 0;  // rows this block has staged so far (same in every thread)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 te = tiles[t];
         __syncthreads();
@@ -812,7 +826,6 @@ __global__ void __launch_bounds__(128) step_kernel_staged(const InstDesc* __rest
         const int x0 = te.z, y0 = te.w;
         const int rows = min(H, sd.ny - y0);
         if ((sd.nx % chunk_elems<T>()) != 0) {
-            // rows not 16-byte aligned: direct loads
             for (int r = 0; r < rows; ++r) {
                 const int x = x0 + 2 * (int)threadIdx.x;
                 for (int v = 0; v < 2; ++v)
@@ -823,23 +836,36 @@ __global__ void __launch_bounds__(128) step_kernel_staged(const InstDesc* __rest
             }
             continue;
         }
-#pragma unroll
-        for (int r = 0; r < STAGES - 1; ++r) {
-            if (r < rows) staged_issue<ST>(sd, buf + (r % STAGES) * 13 * SEG, x0, W, y0 + r, parity);
-            cp_async_commit();
-        }
+        const uint32_t base = seq;
+        int issued = 0;  // rows of this strip issued so far (meaningful in thread 0)
+        if (threadIdx.x == 0)
+            for (; issued < TSTAGES - 1 && issued < rows; ++issued)
+                tma_issue<ST>(sd, buf, bars, base + issued, x0, W, y0 + issued, parity);
         for (int r = 0; r < rows; ++r) {
-            const int rn = r + STAGES - 1;
-            if (rn < rows) staged_issue<ST>(sd, buf + (rn % STAGES) * 13 * SEG, x0, W, y0 + rn, parity);
-            cp_async_commit();
-            cp_async_wait<STAGES - 1>();
-            __syncthreads();
-            const T* stage = buf + (r % STAGES) * 13 * SEG;
+            if (threadIdx.x == 0 && issued < rows && issued < r + TSTAGES) {
+                tma_issue<ST>(sd, buf, bars, base + issued, x0, W, y0 + issued, parity);
+                ++issued;
+            }
+            const uint32_t g = base + r;
+            const bool ok = mbar_wait_bounded(&bars[g % TSTAGES], (g / TSTAGES) & 1u);
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land: record it, wait (bounded) for what this
+                // block still has in flight, and leave
+                if (threadIdx.x == 0) {
+                    atomicExch(&g_step_status, 1);
+                    for (int q = r; q < issued; ++q) {
+                        const uint32_t gq = base + q;
+                        (void)mbar_wait_bounded(&bars[gq % TSTAGES], (gq / TSTAGES) & 1u);
+                    }
+                }
+                return;
+            }
+            const T* stage = buf + (size_t)(g % TSTAGES) * 13 * SEG;
             if (parity) staged_row<ST, 1>(sd, stage, x0, W, y0 + r);
             else staged_row<ST, 0>(sd, stage, x0, W, y0 + r);
             __syncthreads();
         }
-        cp_async_wait<0>();
+        seq += rows;
     }
 }
 

@@ -128,6 +128,8 @@ struct lbm_domain {
     lbm_params params{};
     bool have_params = false;
     int64_t step = 0;
+    double u_seep = 0.0;              // lumped TM: current seepage speed
+    double last_iop = 0.0;            // IOP of the last steady-state check
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
     std::vector<int4> htiles;         // host copy of the tile list
     lbm_batch* batch = nullptr;       // batch this domain belongs to, if any
@@ -452,6 +454,7 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     h.inlet_lo = d->info.inlet_lo;
     h.inlet_width = d->info.inlet_width > 0 ? d->info.inlet_width : 1;
     h.eye_normals = d->info.eye_normals;
+    h.outlet_axis = d->info.outlet_axis;
     h.arc_xc = d->info.arc_xc;
     h.arc_yc = d->info.arc_yc;
     h.fscale = precision == LBM_F16DEV ? 4096.0f : 1.0f;
@@ -498,6 +501,8 @@ static bool finite_all(const lbm_params& p) {
     return true;
 }
 
+static void update_seepage(lbm_domain* d, double iop);
+
 // validates p and derives the descriptor's parameter fields (no upload)
 static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     if (!d || !p) return fail(LBM_EINVAL, "null argument");
@@ -509,6 +514,10 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     if (p->g_beta != 0.0 && std::fabs(gn - 1.0) > 1e-9) return fail(LBM_EINVAL, "g_dir must be a unit vector");
     if (p->porosity < 0.0 || p->porosity > 1.0) return fail(LBM_EINVAL, "porosity must lie in [0, 1]");
     if (p->rho0 < 0.0 || p->dx_m < 0.0 || p->dt_s < 0.0) return fail(LBM_EINVAL, "negative unit scale");
+    if (p->tm_model != 0 && p->tm_model != 1) return fail(LBM_EINVAL, "tm_model must be 0 or 1");
+    if (p->tm_model == 1 && !(std::isfinite(p->h_tm) && p->h_tm > 0.0))
+        return fail(LBM_EINVAL, "the lumped TM needs a positive thickness h_tm");
+    d->h.tm_model = p->tm_model;
     Phys<double>& h = d->h.pd;
     h.omega = 1.0 / p->tau;
     h.omegaT = 1.0 / p->tau_T;
@@ -544,16 +553,27 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     f.drive_x = (float)h.drive_x;
     f.drive_y = (float)h.drive_y;
     f.kwss = (float)h.kwss;
+    h.u_seep = d->u_seep;
+    f.u_seep = (float)d->u_seep;
     d->params = *p;
     return LBM_OK;
 }
 
 extern "C" lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
+    if (!d || !p) return fail(LBM_EINVAL, "null argument");
+    const bool changed = !d->have_params || std::memcmp(&d->params, p, sizeof(lbm_params)) != 0;
     lbm_status st = apply_params(d, p);
     if (st != LBM_OK) return st;
     const bool first = !d->have_params;
     d->have_params = true;
     if (first) return lbm_reset_state(d);
+    if (changed) {
+        // a new parameter set starts a new approach to steady state: the old
+        // velocity snapshot no longer measures convergence, and the lumped
+        // meshwork's seepage speed follows the new K, nu or h_tm at once
+        d->h.snap_valid = 0;
+        update_seepage(d, d->last_iop);
+    }
     return upload_desc(d);
 }
 
@@ -564,6 +584,10 @@ extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
     d->h.Tshift = lowp ? (float)(0.25 * d->params.T0) : 0.0f;
     d->h.snap_valid = 0;
     d->h.parity = 0;
+    d->u_seep = 0.0;
+    d->last_iop = d->params.p_out;
+    d->h.pd.u_seep = 0.0;
+    d->h.pf.u_seep = 0.0f;
     lbm_status st = upload_desc(d);
     if (st != LBM_OK) return st;
     DISPATCH(d->prec, init_kernel, d->d_desc, d->params.noise_amp, d->params.seed);
@@ -641,11 +665,18 @@ extern "C" lbm_status lbm_step(lbm_domain* d, int64_t nsteps) {
     return LBM_OK;
 }
 
+static lbm_status check_step_status() {
+    int st = 0;
+    CK(take_step_status(&st));
+    if (st != 0) return fail(LBM_ECUDA, "a staged population copy did not complete; results are invalid");
+    return LBM_OK;
+}
+
 static lbm_status fetch_obs(lbm_domain* d, double* o) {
     CK(launch_finalize(d->d_desc, 1, d->stream));
     CK(cudaMemcpyAsync(o, d->d_obs, NOBS * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
     CK(cudaStreamSynchronize(d->stream));
-    return LBM_OK;
+    return check_step_status();
 }
 
 static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out) {
@@ -668,6 +699,20 @@ static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_obs
     out->n_cornea = (int64_t)o[O_N_C];
     out->n_iris = (int64_t)o[O_N_I];
     out->nan_flag = o[O_NAN] != 0.0;
+    out->u_seep = d->h.tm_model == 1 ? d->h.pd.u_seep : 0.0;
+}
+
+// Lumped TM (Sec. 2.3): Darcy's law across the meshwork gives the seepage
+// speed for the observed IOP, u_s = K (iop - p_out) / (nu h_tm) (kinematic
+// pressure, nu from Eq. 10); it applies from the next step on.
+static void update_seepage(lbm_domain* d, double iop) {
+    d->last_iop = iop;
+    if (d->h.tm_model != 1) return;
+    const lbm_params& p = d->params;
+    const double nu = (2.0 * p.tau - 1.0) / 6.0;
+    d->u_seep = p.K_tm * (iop - p.p_out) / (nu * p.h_tm);
+    d->h.pd.u_seep = d->u_seep;
+    d->h.pf.u_seep = (float)d->u_seep;
 }
 
 extern "C" lbm_status lbm_read_observables(lbm_domain* d, lbm_observables* out) {
@@ -700,12 +745,12 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
         taken += check_every;
         if (steps_out) *steps_out = taken;
         if (o[O_NAN] != 0.0) return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
-        if (!had_snap) {
+        update_seepage(d, o[O_IOP]);
+        if (d->h.tm_model == 1 || !had_snap) {
             d->h.snap_valid = 1;
             if ((st = upload_desc(d)) != LBM_OK) return st;
-        } else if (o[O_RESID] < tol) {
-            return LBM_OK;
         }
+        if (had_snap && o[O_RESID] < tol) return LBM_OK;
     }
     return fail(LBM_ENOTCONVERGED, "not steady after %lld steps", (long long)taken);
 }
@@ -741,6 +786,7 @@ struct StateHeader {
     int32_t nx, ny, prec, snap_valid;
     int64_t step, npad;
     double Tshift;
+    double u_seep;
     lbm_params params;
 };
 }  // namespace
@@ -764,6 +810,7 @@ extern "C" lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes
     hd.step = d->step;
     hd.npad = d->L.npad;
     hd.Tshift = d->h.Tshift;
+    hd.u_seep = d->u_seep;
     hd.params = d->params;
     std::memcpy(host_buf, &hd, sizeof(hd));
     CK(cudaMemcpyAsync(static_cast<char*>(host_buf) + sizeof(hd), d->h.pops,
@@ -780,6 +827,7 @@ extern "C" lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t
     if (std::memcmp(hd.magic, "LBMSTAT1", 8) != 0 || hd.nx != d->nx || hd.ny != d->ny ||
         hd.prec != d->prec || hd.npad != d->L.npad)
         return fail(LBM_EINVAL, "checkpoint does not match this domain");
+    d->u_seep = hd.u_seep;
     lbm_status st = apply_params(d, &hd.params);  // no reset: populations come from the buffer
     if (st != LBM_OK) return st;
     d->have_params = true;
@@ -1077,12 +1125,14 @@ extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
     CK(cudaMemcpyAsync(b->hobs.data(), b->d_obs, b->hobs.size() * sizeof(double), cudaMemcpyDeviceToHost,
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    if ((st = check_step_status()) != LBM_OK) return st;
     for (int k = 0; k < n; ++k) {
         lbm_domain* m = b->members[k];
         // the observing step ran at step - 1 (pre-collision state of that step)
         fill_obs(m, b->hobs.data() + (size_t)k * NOBS, m->step - 1, &m->last_obs);
         m->have_last_obs = true;
-        if (!m->h.snap_valid) {
+        update_seepage(m, m->last_obs.iop);
+        if (!m->h.snap_valid || m->h.tm_model == 1) {
             m->h.snap_valid = 1;
             if ((st = upload_desc(m)) != LBM_OK) return st;
         }
@@ -1139,8 +1189,8 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
     if (steps_per_candidate < 2) return fail(LBM_EINVAL, "steps_per_candidate must be >= 2");
     if (b->members.empty()) return fail(LBM_EINVAL, "empty batch");
     static const lbm_launch cand[] = {
-        {64, 1, 4, 0}, {128, 1, 4, 0}, {32, 2, 4, 0}, {128, 1, 2, 0}, {64, 2, 2, 0},
-        {64, 1, 8, 0}, {256, 1, 2, 0}, {64, 1, 4, 16}, {128, 1, 2, 8}, {32, 4, 2, 0}};
+        {128, 2, 2, 0}, {64, 2, 2, 0}, {128, 2, 1, 0}, {64, 2, 4, 0}, {128, 1, 4, 0},
+        {128, 1, 8, 0}, {256, 1, 8, 0}, {128, 1, 16, 0}, {128, 2, 2, 8}, {64, 4, 1, 0}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

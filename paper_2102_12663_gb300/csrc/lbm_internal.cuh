@@ -49,6 +49,7 @@ struct Phys {
     R p_out;
     R drive_x, drive_y;
     R kwss;               // -(1 - 1/(2 tau))
+    R u_seep;             // lumped TM: seepage speed out of the outlets
 };
 
 // Everything a kernel needs to update one problem instance.  Lives in device
@@ -67,6 +68,8 @@ struct InstDesc {
     int32_t snap_valid;
     int32_t inlet_dir_x, inlet_dir_y, inlet_profile, inlet_lo, inlet_width;
     int32_t eye_normals;
+    int32_t tm_model;    // 0 porous TM cells, 1 lumped TM (seepage-velocity outlets)
+    int32_t outlet_axis; // outlets drain along x (0) or y (1)
     int32_t pad0;
     double arc_xc, arc_yc;
     Phys<double> pd;
@@ -87,16 +90,9 @@ struct Shape {
     int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = (tw / V) x bh threads
 };
 
-// Cells per thread along x of the FP32-arithmetic kernels: 2 selects the
-// cell-pair path (vector loads and stores, warp shuffles), 1 the
-// software-pipelined one-cell-per-thread path.  The FP64 kernel always takes
-// single cells.
-#ifndef LBM_PAIR_CELLS
-#define LBM_PAIR_CELLS 2
-#endif
-__host__ __device__ constexpr int cells_per_thread(int precision) {
-    return precision == 0 ? 1 : LBM_PAIR_CELLS;
-}
+// Cells per thread along x: the FP32-arithmetic kernels take cell pairs
+// (vector loads and stores, warp shuffles), the FP64 kernel single cells.
+__host__ __device__ constexpr int cells_per_thread(int precision) { return precision == 0 ? 1 : 2; }
 
 // ---- storage traits --------------------------------------------------------
 struct StF64 {
@@ -201,6 +197,9 @@ struct StepPlan {
     size_t smem;
 };
 StepPlan step_plan(int precision, bool obs, Shape shape);
+// status word of the staged kernels: 0, or 1 after a staged copy did not
+// complete in time (read and cleared)
+cudaError_t take_step_status(int* status);
 StepPlan step_plan_f64(bool obs, Shape shape);
 StepPlan step_plan_lp(int precision, bool obs, Shape shape);
 

@@ -1,6 +1,6 @@
 // FP32-arithmetic instantiations of the fused step: FP32 storage and the two
 // 16-bit deviation storages (FP16 scaled, BF16).  Plain steps with one row of
-// threads per block take the cp.async-staged kernel; observing steps and
+// threads per block take the TMA-staged kernel; observing steps and
 // other shapes take the direct kernel.
 #include "kernel_body.cuh"
 
@@ -10,9 +10,17 @@ template <class ST>
 static StepPlan plan_t(bool obs, Shape shape) {
     StepPlan p;
     if (!obs && shape.bh == 1) {
-        p.func = reinterpret_cast<const void*>(&step_kernel_staged<ST>);
+        using T = typename ST::T;
+        p.func = reinterpret_cast<const void*>(&step_kernel_tma<ST>);
         p.block = dim3(shape.tw / 2, 1);
-        p.smem = staged_smem_bytes<typename ST::T>(shape.tw);
+        p.smem = (size_t)TSTAGES * 13 * seg_elems<T>(shape.tw) * sizeof(T);
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(reinterpret_cast<const void*>(&step_kernel_tma<ST>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)TSTAGES * 13 * seg_elems<T>(256) * sizeof(T)));
+            attr_set = true;
+        }
     } else {
         p.func = obs ? reinterpret_cast<const void*>(&step_kernel<ST, true>)
                      : reinterpret_cast<const void*>(&step_kernel<ST, false>);
@@ -30,4 +38,14 @@ StepPlan step_plan_lp(int precision, bool obs, Shape shape) {
     }
 }
 
+}  // namespace lbm
+
+namespace lbm {
+// Reads and clears the status word of the staged kernels (0 = fine).
+cudaError_t take_step_status(int* status) {
+    cudaError_t e = cudaMemcpyFromSymbol(status, g_step_status, sizeof(int));
+    if (e != cudaSuccess || *status == 0) return e;
+    const int zero = 0;
+    return cudaMemcpyToSymbol(g_step_status, &zero, sizeof(int));
+}
 }  // namespace lbm

@@ -49,6 +49,7 @@ class GeometryInfo(ctypes.Structure):
         ("inlet_dir_x", ctypes.c_int32), ("inlet_dir_y", ctypes.c_int32),
         ("inlet_profile", ctypes.c_int32), ("inlet_lo", ctypes.c_int32),
         ("inlet_width", ctypes.c_int32), ("eye_normals", ctypes.c_int32),
+        ("outlet_axis", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("arc_xc", ctypes.c_double), ("arc_yc", ctypes.c_double),
     ]
 
@@ -64,6 +65,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("dx_m", ctypes.c_double), ("dt_s", ctypes.c_double), ("rho0", ctypes.c_double),
         ("p_sc_pa", ctypes.c_double),
+        ("tm_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("h_tm", ctypes.c_double),
     ]
 
 
@@ -77,6 +79,7 @@ class Observables(ctypes.Structure):
         ("wss_iris_pa", ctypes.c_double), ("residual", ctypes.c_double),
         ("n_fluid", ctypes.c_int64), ("n_cornea", ctypes.c_int64), ("n_iris", ctypes.c_int64),
         ("nan_flag", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("u_seep", ctypes.c_double),
     ]
 
 
@@ -225,6 +228,8 @@ def make_params(p: dict) -> Params:
     P.dt_s = p.get("dt_s", 0.0)
     P.rho0 = p.get("rho0", 0.0)
     P.p_sc_pa = p.get("p_sc_pa", 0.0)
+    P.tm_model = int(p.get("tm_model", 0))
+    P.h_tm = float(p.get("h_tm", 0.0))
     return P
 
 

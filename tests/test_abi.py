@@ -43,7 +43,8 @@ def test_struct_layout_matches_header(tmp_path):
     body = "".join(f'printf("{k} %zu\\n", sizeof({k}));' for k in structs)
     fields = [("lbm_params", "seed"), ("lbm_params", "p_sc_pa"), ("lbm_observables", "nan_flag"),
               ("lbm_geometry_desc", "chamber_angle_deg"), ("lbm_geometry_desc", "host_mask"),
-              ("lbm_geometry_info", "arc_xc")]
+              ("lbm_geometry_info", "arc_xc"), ("lbm_params", "h_tm"),
+              ("lbm_observables", "u_seep")]
     body += "".join(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));' for s, f in fields)
     c = tmp_path / "probe.c"
     c.write_text(f'#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){{{body}return 0;}}\n')

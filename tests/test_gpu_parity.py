@@ -282,3 +282,44 @@ def test_full_size_fp32_sampled_windows():
         assert ef <= 1e-5 and eg <= 1e-5, (x0, y0, ef, eg)
     o = dom.observables()
     assert o["nan_flag"] == 0 and o["n_fluid"] == info["n_fluid"]
+
+
+def _lumped_oracle_checks(ref, params, h_tm, checks, every):
+    """The host side of the lumped meshwork (Sec. 2.3) in the oracle, in the
+    cadence of lbm_run_to_steady: every-1 plain steps, one observed step, then
+    the seepage speed for the observed IOP."""
+    for _ in range(checks):
+        ref.run(every - 1)
+        o = ref.observe()
+        ref.step()
+        params.u_seep = O.seepage_velocity(params, o["iop"], h_tm)
+
+
+def test_lumped_tm_eye_fp64_parity():
+    """Paper's lumped meshwork on the eye (no drag in the TM cells, seepage
+    velocity at the outlets fed back from the IOP every 50 steps)."""
+    h_tm = 3.0
+    dom, ref, pp = eye_pair(160, 80, "f64", tm_model=1, h_tm=h_tm)
+    P = O.make_params(**pp)
+    ref.params = P
+    st, steps = dom.run_to_steady(0.0, check_every=50, max_steps=400)
+    assert steps == 400
+    _lumped_oracle_checks(ref, P, h_tm, 8, 50)
+    assert rel_err(dom, ref) <= 1e-12
+    o = dom.observables()
+    assert o["u_seep"] == pytest.approx(P.u_seep, rel=1e-12) and o["u_seep"] > 0
+
+
+def test_lumped_tm_column_reaches_darcy_iop_on_gpu():
+    m, d = W.darcy_column(12, 0, 12, 2)
+    u, K, h, tau = 1e-4, 0.5, 4.0, 0.8
+    geo = dict(mask=m, **{k: v for k, v in d.items() if k not in ("nx", "ny")})
+    for prec, tol_rel in (("f64", 1e-8), ("f32", 1e-4)):
+        dom = lbm.Domain(geo, precision=prec)
+        dom.set_params(dict(tau=tau, u_in_max=u, K_tm=K, tm_model=1, h_tm=h))
+        st, steps = dom.run_to_steady(1e-13 if prec == "f64" else 1e-9, check_every=50,
+                                      max_steps=40000)
+        o = dom.observables()
+        nu = (2 * tau - 1) / 6
+        assert o["iop"] == pytest.approx(nu * h * u / K, rel=tol_rel)
+        assert o["q_out"] == pytest.approx(o["q_in"], rel=tol_rel)

@@ -332,3 +332,25 @@ def test_eye_geometry(angle):
     cols = np.where((m == O.FLUID).any(axis=0))[0]
     assert cols.min() >= xa and cols.max() <= nx - 1 - xa
     assert abs((cols.max() - cols.min() + 1) - 2 * a) <= 2.0
+
+
+def test_lumped_tm_steady_state_obeys_darcy_law():
+    """Lumped meshwork of Sec. 2.3: with the seepage velocity fed back from the
+    IOP, the steady state balances inflow and outflow and the IOP satisfies
+    Darcy's law (Eq. 4) across the meshwork, IOP - p_0 = mu h Q / (K A)."""
+    m, d = W.darcy_column(12, 0, 12, 2)
+    g = O.mask_geom(d["nx"], d["ny"], 0, 1, d["inlet_dir"], d["inlet_profile"])
+    u, K, h, tau = 1e-4, 0.5, 4.0, 0.8
+    P = O.make_params(tau=tau, u_in_max=u, K_tm=K, tm_model=1)
+    s = O.State(g, P, m)
+    nu = (2 * tau - 1) / 6
+    for _ in range(300):
+        s.run(49)
+        o = s.observe()
+        s.step()
+        P.u_seep = O.seepage_velocity(P, o["iop"], h)
+    o = s.observe()
+    qi, qo = s.step()
+    assert o["iop"] == pytest.approx(nu * h * u / K, rel=1e-8)
+    assert P.u_seep == pytest.approx(u, rel=1e-8)
+    assert qo == pytest.approx(qi, rel=1e-8)
