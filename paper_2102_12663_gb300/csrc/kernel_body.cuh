@@ -656,11 +656,11 @@ __device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST
         const int jj = PAR == 0 ? j : j - ex(i);
         const T* src = stage + pl * SEG + jj;
         if (heat) {
-            a[k] = ST::ldT(src, sd);
-            b[k] = ST::ldT(src + 1, sd);
+            a[k] = ST::sldT(src, sd);
+            b[k] = ST::sldT(src + 1, sd);
         } else {
-            a[k] = ST::ldf(src, sd);
-            b[k] = ST::ldf(src + 1, sd);
+            a[k] = ST::sldf(src, sd);
+            b[k] = ST::sldf(src + 1, sd);
         }
     }
     const bool interior = (m2 & 0x0E0Eu) == 0u;

@@ -103,83 +103,99 @@ struct StF64 {
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
 };
+// The FP32-arithmetic storages read populations through L2 only (each slot
+// is read once per step, so L1 would only hold dead lines) and write them as
+// streaming stores (evict-first: the next step reads them from DRAM anyway).
 struct StF32 {
     using T = float;
     using R = float;
-    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return *p; }
-    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { *p = v; }
-    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
-    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { __stcs(p, v); }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { __stcs(p, v); }
     // two neighbouring cells (p 8-byte aligned)
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc&) {
-        return *reinterpret_cast<const float2*>(p);
+        return __ldcg(reinterpret_cast<const float2*>(p));
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc&) {
-        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+        __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) { return ldf2(p, d); }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) { stf2(p, a, b, d); }
+    // decode a value staged in shared memory (plain load: not a global address)
+    static __device__ __forceinline__ R sldf(const T* p, const InstDesc&) { return *p; }
+    static __device__ __forceinline__ R sldT(const T* p, const InstDesc&) { return *p; }
 };
 struct StF16 {
     using T = __half;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
-        return __half2float(*p) * d.finv;
+        return __half2float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        *p = __float2half_rn(v * d.fscale);
+        __stcs(p, __float2half_rn(v * d.fscale));
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __half2float(*p) * d.finv + d.Tshift;
+        return __half2float(__ldcg(p)) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        *p = __float2half_rn((v - d.Tshift) * d.fscale);
+        __stcs(p, __float2half_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
-        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
         return make_float2(v.x * d.finv, v.y * d.finv);
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
-        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * d.fscale, b * d.fscale);
+        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(a * d.fscale, b * d.fscale));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
-        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
         return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
     }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        *reinterpret_cast<__half2*>(p) =
-            __floats2half2_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale);
+        __stcs(reinterpret_cast<__half2*>(p),
+               __floats2half2_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
+    }
+    static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) { return __half2float(*p) * d.finv; }
+    static __device__ __forceinline__ R sldT(const T* p, const InstDesc& d) {
+        return __half2float(*p) * d.finv + d.Tshift;
     }
 };
 struct StBF16 {
     using T = __nv_bfloat16;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
-        return __bfloat162float(*p) * d.finv;
+        return __bfloat162float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        *p = __float2bfloat16_rn(v * d.fscale);
+        __stcs(p, __float2bfloat16_rn(v * d.fscale));
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __bfloat162float(*p) * d.finv + d.Tshift;
+        return __bfloat162float(__ldcg(p)) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        *p = __float2bfloat16_rn((v - d.Tshift) * d.fscale);
+        __stcs(p, __float2bfloat16_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
         return make_float2(v.x * d.finv, v.y * d.finv);
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a * d.fscale, b * d.fscale);
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a * d.fscale, b * d.fscale));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
         return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
     }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        *reinterpret_cast<__nv_bfloat162*>(p) =
-            __floats2bfloat162_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale);
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p),
+               __floats2bfloat162_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
+    }
+    static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) {
+        return __bfloat162float(*p) * d.finv;
+    }
+    static __device__ __forceinline__ R sldT(const T* p, const InstDesc& d) {
+        return __bfloat162float(*p) * d.finv + d.Tshift;
     }
 };
 

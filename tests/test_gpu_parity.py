@@ -323,3 +323,28 @@ def test_lumped_tm_column_reaches_darcy_iop_on_gpu():
         nu = (2 * tau - 1) / 6
         assert o["iop"] == pytest.approx(nu * h * u / K, rel=tol_rel)
         assert o["q_out"] == pytest.approx(o["q_in"], rel=tol_rel)
+
+
+@pytest.mark.parametrize("prec,unit_roundoff", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_eye_sixteen_bit_storage(prec, unit_roundoff):
+    """16-bit deviation storage against the FP64 oracle after n = 100 steps:
+    every step re-rounds each stored population once (relative unit roundoff u
+    of the format), so the deviation stays within a few u sqrt(n) of the
+    population scale; a wrong slot or scale would be off by O(1)."""
+    n = 100
+    dom, ref, _ = eye_pair(160, 80, prec)
+    dom.step(n)
+    ref.run(n)
+    assert rel_err(dom, ref) <= 4.0 * unit_roundoff * n ** 0.5
+
+
+def test_supine_eye_mirror_symmetry_fp32():
+    """The supine eye without noise stays mirror-symmetric on the FP32 path
+    (cell pairs, shuffled x-shifted links in both directions)."""
+    dom, ref, _ = eye_pair(160, 80, "f32", g_dir=W.SUPINE, noise_amp=0.0)
+    dom.step(600)
+    u, p, T = (t.cpu().numpy() for t in dom.fields())
+    ux, uy = u[0], u[1]
+    assert np.abs(ux + ux[:, ::-1]).max() <= 1e-5 * np.abs(ux).max()
+    assert np.abs(uy - uy[:, ::-1]).max() <= 1e-5 * np.abs(uy).max()
+    assert np.abs(T - T[:, ::-1]).max() <= 1e-5
