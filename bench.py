@@ -238,11 +238,16 @@ def run_gpu(args):
             bench_step()
         stream.synchronize()
 
-        # dominant kernel alone: average duration of the plain fused step
+        # dominant kernel alone, as the bench step launches it: a dataflow
+        # launch of CHECK - 1 steps (or, stepping one launch per step, the
+        # average of 200 graph-replayed single steps)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nk = 200
+        flow = LAUNCH.get("stepping", lbm.STEP_FLOW) == lbm.STEP_FLOW
+        steps_per_launch = CHECK - 1 if flow else 1
+        nk = 5 if flow else 200
         ev0.record(stream)
-        dom.step(nk)
+        for _ in range(nk if flow else 1):
+            dom.step(steps_per_launch if flow else nk)
         ev1.record(stream)
         ev1.synchronize()
         kernel_ms = ev0.elapsed_time(ev1) / nk
@@ -286,13 +291,15 @@ def run_gpu(args):
     value = weak_scaling_mlups(n_active, args.steps, world, t_max)
     e2e_value = weak_scaling_mlups(n_active, args.steps, world, e2e_s * 1e3)
     peak, peak_kind = hbm_peak()
-    achieved = step_bytes / (kernel_ms * 1e-3) / 1e9
+    bytes_per_launch = steps_per_launch * step_bytes
+    achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     traffic = None
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if tr.get("kernel_hash") == kernel_hash() and tr.get("launch") == LAUNCH:
-            traffic = tr.get("dram_bytes_per_launch")
+            # DRAM bytes grow with the steps a launch covers
+            traffic = tr["dram_bytes_per_step"] * steps_per_launch
     except Exception:
         pass
     cpu = None
@@ -316,12 +323,15 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "kernel": "step_kernel<StF32,false>", "kernel_ms": kernel_ms,
-                         "algorithmic_bytes_per_launch": step_bytes},
+                         "kernel": "step_kernel_flow<StF32>" if flow else "step_kernel<StF32,false>",
+                         "kernel_ms": kernel_ms, "steps_per_launch": steps_per_launch,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (CHECK + 1),
+            # per bench step: the plain steps (one dataflow launch, or CHECK - 1
+            # single launches), the observing step and the finalize kernel
+            "gpu_launches": args.steps * (3 if flow else CHECK + 1),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -331,7 +341,7 @@ def run_gpu(args):
     return 0
 
 
-LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0)
+LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):
@@ -570,7 +580,11 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16", "f64"],
                     help="storage precision for --profile")
     ap.add_argument("--launch", default=None,
-                    help="launch shape for --profile: tile_w,block_rows,rows_per_thread,blocks_per_sm")
+                    help="launch shape for --profile: tile_w,block_rows,rows_per_thread,"
+                         "blocks_per_sm[,stepping[,sweep_steps,sweep_lag]]")
+    ap.add_argument("--profile-steps", type=int, default=1,
+                    help="steps per lbm_step call of the profiling driver (one "
+                         "dataflow launch per call when the shape's stepping is 0)")
     ap.add_argument("--workload", default="fp32", choices=["fp32", "precision", "batch", "serve"],
                     help="fp32: the FP32 4096x2048 throughput line (default); precision, batch, "
                          "serve: the reduced-storage, batching and serving studies")
@@ -595,7 +609,8 @@ def main():
 
 
 def run_profile(args):
-    """A short, fixed sequence of single-step launches for ncu captures."""
+    """A short, fixed sequence of launches for ncu captures: --profile calls
+    of lbm_step with --profile-steps steps each."""
     import torch
 
     from paper_2102_12663_gb300 import lbm
@@ -603,14 +618,14 @@ def run_profile(args):
     dom = lbm.Domain(dict(nx=NX, ny=NY, angle_deg=45.0), precision=args.precision)
     launch = LAUNCH
     if args.launch:
-        launch = dict(zip(("tile_w", "block_rows", "rows_per_thread", "blocks_per_sm"),
-                          (int(v) for v in args.launch.split(","))))
+        launch = dict(zip(("tile_w", "block_rows", "rows_per_thread", "blocks_per_sm", "stepping",
+                           "sweep_steps", "sweep_lag"), (int(v) for v in args.launch.split(","))))
     dom.set_launch(**launch)
     dom.set_params(eye_params())
     for _ in range(args.profile):
-        dom.step(1)
+        dom.step(args.profile_steps)
     torch.cuda.synchronize()
-    print(f"profile driver: {args.profile} steps, {dom.tile_count()} tiles, "
+    print(f"profile driver: {args.profile} x {args.profile_steps} steps, {dom.tile_count()} tiles, "
           f"{dom.step_bytes():.0f} algorithmic bytes per step", flush=True)
     dom.close()
     return 0

@@ -172,12 +172,37 @@ typedef struct lbm_observables {
 } lbm_observables;
 
 /* Launch shape of the fused step kernel: tiles of tile_w x (block_rows *
- * rows_per_thread) cells, one thread per column and row group;
- * blocks_per_sm > 0 selects a persistent grid of that many blocks per SM,
- * 0 one block per tile.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
- * <= 1024, tile area >= 128 cells. */
+ * rows_per_thread) cells, one thread per column (FP64) or column pair (other
+ * storages) and row group.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
+ * <= 256, tile area >= 128 cells.
+ *
+ * stepping selects how lbm_step advances a domain:
+ *   LBM_STEP_FLOW: one cooperative launch covers all the steps of the call.  No
+ *     grid-wide barrier separates them: a tile starts step s as soon as it
+ *     and its eight neighbour tiles have finished step s - 1 (each link
+ *     reaches one cell).  The grid is the co-resident block count (capped at
+ *     blocks_per_sm per SM when blocks_per_sm > 0).  The steps are issued in
+ *     sweeps of sweep_steps steps (0 or 1: one step at a time, at most 8): a
+ *     wavefront over the tile rows with step k + 1 of the sweep sweep_lag
+ *     tile rows behind step k (0: 8 rows; otherwise at least 2).  Step k + 1
+ *     then reads what step k wrote while it is still in L2.  Grids periodic
+ *     in y sweep one step at a time.  Falls back to LBM_STEP_PER_LAUNCH on a
+ *     device without cooperative launches.
+ *   LBM_STEP_PER_LAUNCH: one launch per step, replayed from a CUDA graph of
+ *     32 steps; blocks_per_sm > 0 selects a grid of that many blocks per SM,
+ *     0 one block per tile.  With FP32 arithmetic, shapes with block_rows 1
+ *     take a kernel that stages population rows in shared memory by bulk
+ *     copies; its interior collision rounds differently in the last bit.
+ * The dataflow kernel (any sweep) and the per-step direct kernel give
+ * bit-identical populations.  Observing steps and batches always take one
+ * launch per step. */
+enum { LBM_STEP_FLOW = 0, LBM_STEP_PER_LAUNCH = 1 };
+
 typedef struct lbm_launch {
     int32_t tile_w, block_rows, rows_per_thread, blocks_per_sm;
+    int32_t stepping;    /* LBM_STEP_FLOW or LBM_STEP_PER_LAUNCH */
+    int32_t sweep_steps; /* LBM_STEP_FLOW: steps per wavefront sweep, 0..8 */
+    int32_t sweep_lag;   /* LBM_STEP_FLOW: tile rows between a sweep's steps */
 } lbm_launch;
 
 typedef struct lbm_domain lbm_domain;

@@ -54,12 +54,37 @@ __device__ __forceinline__ constexpr double wgt(int i) {
     return i == 0 ? K_W0 : (i <= 4 ? K_W1 : K_W5);
 }
 
+// Arithmetic rounded one operation at a time: no multiply and add of an Rn
+// expression is ever fused, so a function written in Rn computes the same
+// bits in every kernel that inlines it (the compiler's contraction choices
+// depend on the surrounding code).  Operands of an operation must both be Rn;
+// mixing in a plain R or double does not compile.
 template <class R>
-__device__ __forceinline__ R pressure_from(R sum18, R S0) {
-    // Eq. 9: p = [sum_{i>=1} f_i + S_0(u)] / (4 sigma)
-    if constexpr (sizeof(R) == 8) return (sum18 + S0) / R(4.0 * K_SIGMA);
-    else return (sum18 + S0) * R(0.6);
-}
+struct Rn {
+    R v;
+    Rn() = default;
+    __host__ __device__ constexpr Rn(R a) : v(a) {}
+    template <class U>
+    __host__ __device__ constexpr explicit Rn(U a) : v(R(a)) {}
+};
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+template <class R>
+__device__ __forceinline__ Rn<R> operator+(Rn<R> a, Rn<R> b) { return Rn<R>(rn_add(a.v, b.v)); }
+template <class R>
+__device__ __forceinline__ Rn<R> operator-(Rn<R> a, Rn<R> b) { return Rn<R>(rn_sub(a.v, b.v)); }
+template <class R>
+__device__ __forceinline__ Rn<R> operator*(Rn<R> a, Rn<R> b) { return Rn<R>(rn_mul(a.v, b.v)); }
+template <class R>
+__device__ __forceinline__ Rn<R> operator/(Rn<R> a, Rn<R> b) { return Rn<R>(rn_div(a.v, b.v)); }
+template <class R>
+__device__ __forceinline__ Rn<R> operator-(Rn<R> a) { return Rn<R>(-a.v); }
 
 template <class R>
 __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPART], double* out) {
@@ -138,12 +163,16 @@ __device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, type
 }
 
 // Everything after the load: observables, collision, boundary rules, stores.
+// The arithmetic runs in Rn<R> (each operation rounded on its own), so the
+// update is the same function of the loaded populations in every kernel that
+// inlines it.
 template <class ST, bool OBS, int PAR>
 __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
-                                          const typename ST::R* f, const typename ST::R* g,
+                                          const typename ST::R* fin, const typename ST::R* gin,
                                           uint8_t m, int mode, double* acc) {
     using T = typename ST::T;
     using R = typename ST::R;
+    using E = Rn<R>;
     const int nx = d.nx, ny = d.ny;
     int nb[9];
     neighbours(d, x, y, nb);
@@ -155,19 +184,25 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     const Phys<R>& ph = phys<R>(d);
     const int type = m & TYPE_BITS;
     if (type > POROUS) return;
+    E f[9], g[4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fin[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = gin[i];
 
     // ---- moments, Eq. 9 and Eq. 13 ------------------------------------------
-    const R ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    const R uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-    const R usq = ux * ux + uy * uy;
-    const R S0 = R(K_W0) * (R(-1.5) * usq);
-    const R sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    const R p = pressure_from<R>(sum18, S0);
-    const R Tm = g[0] + g[1] + g[2] + g[3];
+    const E ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const E uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    const E usq = ux * ux + uy * uy;
+    const E S0 = E(K_W0) * (E(-1.5) * usq);
+    const E sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    // p = [sum_{i>=1} f_i + S_0(u)] / (4 sigma); the FP32 form multiplies by 0.6
+    const E p = sizeof(R) == 8 ? (sum18 + S0) / E(4.0 * K_SIGMA) : (sum18 + S0) * E(0.6);
+    const E Tm = g[0] + g[1] + g[2] + g[3];
 
     // e_i . u for i = 0..8
-    R eu[9];
-    eu[0] = R(0);
+    E eu[9];
+    eu[0] = E(0.0);
     eu[1] = ux;
     eu[2] = uy;
     eu[3] = -ux;
@@ -178,12 +213,12 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     eu[8] = ux - uy;
 
     // equilibrium, Eqs. 7-8
-    R feq[9];
-    feq[0] = R(-4.0 * K_SIGMA) * p + S0;
+    E feq[9];
+    feq[0] = E(-4.0 * K_SIGMA) * p + S0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const R Si = R(wgt(i)) * (R(3.0) * eu[i] + R(4.5) * eu[i] * eu[i] - R(1.5) * usq);
-        feq[i] = (i <= 4 ? R(K_LAMBDA) : R(K_GAMMA)) * p + Si;
+        const E Si = E(wgt(i)) * (E(3.0) * eu[i] + E(4.5) * eu[i] * eu[i] - E(1.5) * usq);
+        feq[i] = (i <= 4 ? E(K_LAMBDA) : E(K_GAMMA)) * p + Si;
     }
 
     // neighbour types (only next to a boundary)
@@ -200,13 +235,13 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     // ---- observables of the pre-collision state -----------------------------
     if (OBS) {
         if (mode & OBS_STATS) {
-            acc[P_MASS] += (double)sum18;
-            const double sp = sqrt((double)usq);
-            acc[P_PEAK] = fmax(acc[P_PEAK], sp);
+            acc[P_MASS] += (double)sum18.v;
+            // max of |u|^2; the fold takes one square root (sqrt is monotone)
+            acc[P_PEAK] = fmax(acc[P_PEAK], (double)usq.v);
             if (type == FLUID) {
-                acc[P_SUM_P] += (double)p;
+                acc[P_SUM_P] += (double)p.v;
                 acc[P_N_FLUID] += 1.0;
-                if (!isfinite((double)p)) acc[P_NAN] += 1.0;
+                if (!isfinite((double)p.v)) acc[P_NAN] += 1.0;
                 if (bnd) {
                     bool hit_c = false, hit_h = false;
                     double ac_x = 0.0, ac_y = 0.0, ah_x = 0.0, ah_y = 0.0;
@@ -218,10 +253,10 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                     }
                     if (hit_c || hit_h) {
                         // non-equilibrium stress sigma = -(1 - 1/(2 tau)) sum e e (f - feq)
-                        const double d1 = (double)(f[1] - feq[1]), d2 = (double)(f[2] - feq[2]);
-                        const double d3 = (double)(f[3] - feq[3]), d4 = (double)(f[4] - feq[4]);
-                        const double d5 = (double)(f[5] - feq[5]), d6 = (double)(f[6] - feq[6]);
-                        const double d7 = (double)(f[7] - feq[7]), d8 = (double)(f[8] - feq[8]);
+                        const double d1 = (double)(f[1] - feq[1]).v, d2 = (double)(f[2] - feq[2]).v;
+                        const double d3 = (double)(f[3] - feq[3]).v, d4 = (double)(f[4] - feq[4]).v;
+                        const double d5 = (double)(f[5] - feq[5]).v, d6 = (double)(f[6] - feq[6]).v;
+                        const double d7 = (double)(f[7] - feq[7]).v, d8 = (double)(f[8] - feq[8]).v;
                         const double pxx = d1 + d3 + d5 + d6 + d7 + d8;
                         const double pxy = d5 - d6 + d7 - d8;
                         const double pyy = d2 + d4 + d5 + d6 + d7 + d8;
@@ -250,26 +285,26 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         if (mode & (OBS_RESID | OBS_SNAP)) {
             R* U = static_cast<R*>(d.usnap);
             if ((mode & OBS_RESID) && d.snap_valid) {
-                const double dx = (double)ux - (double)U[c];
-                const double dy = (double)uy - (double)U[np + c];
-                acc[P_RESID] = fmax(acc[P_RESID], sqrt(dx * dx + dy * dy));
+                const double dx = (double)ux.v - (double)U[c];
+                const double dy = (double)uy.v - (double)U[np + c];
+                acc[P_RESID] = fmax(acc[P_RESID], dx * dx + dy * dy);
             }
             if (mode & OBS_SNAP) {
-                U[c] = ux;
-                U[np + c] = uy;
+                U[c] = ux.v;
+                U[np + c] = uy.v;
             }
         }
     }
 
     // ---- body force, Eqs. 15-17: F_i = (1/2) e_i . F on the axis links --------
-    const R gb = ph.g_beta * (Tm - ph.T0);
-    const R Fx = ph.drive_x - gb * ph.gx;
-    const R Fy = ph.drive_y - gb * ph.gy;
-    const R F1 = R(0.5) * Fx, F2 = R(0.5) * Fy;
+    const E gb = E(ph.g_beta) * (Tm - E(ph.T0));
+    const E Fx = E(ph.drive_x) - gb * E(ph.gx);
+    const E Fy = E(ph.drive_y) - gb * E(ph.gy);
+    const E F1 = E(0.5) * Fx, F2 = E(0.5) * Fy;
 
     // ---- flow collision, Eq. 6 --------------------------------------------
-    const R om = ph.omega;
-    R fs[9];
+    const E om = E(ph.omega);
+    E fs[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fs[i] = f[i] - om * (f[i] - feq[i]);
     fs[1] = fs[1] + F1;
@@ -280,12 +315,12 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     // ---- Darcy drag in porous cells, Eq. 4 at the mid-step velocity ---------
     // (the lumped meshwork of Sec. 2.3 resolves no flow resistance in the TM)
     if (type == POROUS && d.tm_model == 0) {
-        const R den = ph.den, cK = ph.cK;
-        const R umx = (ux + R(0.5) * Fx) / den;
-        const R umy = (uy + R(0.5) * Fy) / den;
-        const R FDx = -cK * umx;
-        const R FDy = -cK * umy;
-        const R a1 = R(3.0 * K_W1), a5 = R(3.0 * K_W5);
+        const E den = E(ph.den), cK = E(ph.cK);
+        const E umx = (ux + E(0.5) * Fx) / den;
+        const E umy = (uy + E(0.5) * Fy) / den;
+        const E FDx = -cK * umx;
+        const E FDy = -cK * umy;
+        const E a1 = E(3.0 * K_W1), a5 = E(3.0 * K_W5);
         fs[1] = fs[1] + a1 * FDx;
         fs[2] = fs[2] + a1 * FDy;
         fs[3] = fs[3] + a1 * (-FDx);
@@ -297,24 +332,24 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     }
 
     // ---- heat collision, Eqs. 11-12 ----------------------------------------
-    const R omT = ph.omegaT;
-    const R Tq = R(0.25) * Tm;
-    R gs[4];
+    const E omT = E(ph.omegaT);
+    const E Tq = E(0.25) * Tm;
+    E gs[4];
 #pragma unroll
     for (int i = 1; i <= 4; ++i) {
-        const R teq = Tq * (R(1.0) + R(2.0) * eu[i]);
+        const E teq = Tq * (E(1.0) + E(2.0) * eu[i]);
         gs[i - 1] = g[i - 1] - omT * (g[i - 1] - teq);
     }
 
     const bool write = !OBS || (mode & OBS_WRITE);
 
     // ---- stream (AA write pattern) with link-wise boundary rules ----------
-    if (write) ST::stf(P + c, fs[0], d);
+    if (write) ST::stf(P + c, fs[0].v, d);
     double q_in = 0.0, q_out = 0.0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const bool is_bnd = (bnd >> i) & 1u;
-        R v = fs[i];
+        E v = fs[i];
         if (is_bnd) {
             const uint32_t tn = (ntypes >> (4 * (i - 1))) & 15u;
             if (tn == INLET) {
@@ -322,54 +357,54 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                 const int xn = ex(i) == 1 ? xr : (ex(i) == -1 ? xl : x);
                 const int ynb = ey(i) == 1 ? (y == ny - 1 ? 0 : y + 1)
                                            : (ey(i) == -1 ? (y == 0 ? ny - 1 : y - 1) : y);
-                R shape = R(1.0);
+                E shape = E(1.0);
                 if (d.inlet_profile == 1) {
                     const int cg = d.inlet_dir_x == 0 ? xn : ynb;
-                    const R s = (R(cg - d.inlet_lo) + R(0.5)) / R(d.inlet_width);
-                    shape = R(4.0) * s * (R(1.0) - s);
+                    const E s = (E(cg - d.inlet_lo) + E(0.5)) / E(d.inlet_width);
+                    shape = E(4.0) * s * (E(1.0) - s);
                 }
-                const R uin = ph.u_in_max * shape;
-                const R uix = uin * R(d.inlet_dir_x), uiy = uin * R(d.inlet_dir_y);
-                v = fs[i] - R(6.0 * wgt(i)) * (R(ex(i)) * uix + R(ey(i)) * uiy);
-                if (OBS) q_in += (double)(v - fs[i]);
+                const E uin = E(ph.u_in_max) * shape;
+                const E uix = uin * E(d.inlet_dir_x), uiy = uin * E(d.inlet_dir_y);
+                v = fs[i] - E(6.0 * wgt(i)) * (E(ex(i)) * uix + E(ey(i)) * uiy);
+                if (OBS) q_in += (double)(v - fs[i]).v;
             } else if (tn == OUTLET && d.tm_model == 1) {
                 // lumped TM (Sec. 2.3): the seepage velocity, out of the domain
                 // along the outlet axis, as a moving wall
-                const R uwx = d.outlet_axis == 0 ? ph.u_seep * R(ex(i)) : R(0);
-                const R uwy = d.outlet_axis == 1 ? ph.u_seep * R(ey(i)) : R(0);
-                v = fs[i] - R(6.0 * wgt(i)) * (R(ex(i)) * uwx + R(ey(i)) * uwy);
-                if (OBS) q_out += (double)(fs[i] - v);
+                const E uwx = d.outlet_axis == 0 ? E(ph.u_seep) * E(ex(i)) : E(0.0);
+                const E uwy = d.outlet_axis == 1 ? E(ph.u_seep) * E(ey(i)) : E(0.0);
+                v = fs[i] - E(6.0 * wgt(i)) * (E(ex(i)) * uwx + E(ey(i)) * uwy);
+                if (OBS) q_out += (double)(fs[i] - v).v;
             } else if (tn == OUTLET) {
                 // pressure anti-bounce-back: minus f* plus the even part of feq(p_out, u)
-                const R kap = i <= 4 ? R(K_LAMBDA) : R(K_GAMMA);
-                v = -fs[i] + R(2.0) * (kap * ph.p_out +
-                                       R(wgt(i)) * (R(4.5) * eu[i] * eu[i] - R(1.5) * usq));
-                if (OBS) q_out += (double)(fs[i] - v);
+                const E kap = i <= 4 ? E(K_LAMBDA) : E(K_GAMMA);
+                v = -fs[i] + E(2.0) * (kap * E(ph.p_out) +
+                                       E(wgt(i)) * (E(4.5) * eu[i] * eu[i] - E(1.5) * usq));
+                if (OBS) q_out += (double)(fs[i] - v).v;
             }
             // any wall: halfway bounce-back, v = f*_i
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;  // even+stream or odd+boundary
-            if (to_own) ST::stf(P + opp(i) * np + c, v, d);
-            else ST::stf(P + i * np + nb[i], v, d);
+            if (to_own) ST::stf(P + opp(i) * np + c, v.v, d);
+            else ST::stf(P + i * np + nb[i], v.v, d);
         }
     }
 #pragma unroll
     for (int i = 1; i <= 4; ++i) {
         const bool is_bnd = (bnd >> i) & 1u;
-        R v = gs[i - 1];
+        E v = gs[i - 1];
         if (is_bnd) {
             const uint32_t tn = (ntypes >> (4 * (i - 1))) & 15u;
-            if (tn == COLD) v = -gs[i - 1] + R(0.5) * ph.T_cold;
-            else if (tn == HOT) v = -gs[i - 1] + R(0.5) * ph.T_hot;
-            else if (tn == INLET) v = -gs[i - 1] + R(0.5) * ph.T_in;
-            else if (tn == OUTLET) v = -gs[i - 1] + R(0.5) * Tm;
+            if (tn == COLD) v = -gs[i - 1] + E(0.5) * E(ph.T_cold);
+            else if (tn == HOT) v = -gs[i - 1] + E(0.5) * E(ph.T_hot);
+            else if (tn == INLET) v = -gs[i - 1] + E(0.5) * E(ph.T_in);
+            else if (tn == OUTLET) v = -gs[i - 1] + E(0.5) * Tm;
             // adiabatic: bounce-back, zero heat flux
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;
-            if (to_own) ST::stT(P + (8 + opp(i)) * np + c, v, d);
-            else ST::stT(P + (8 + i) * np + nb[i], v, d);
+            if (to_own) ST::stT(P + (8 + opp(i)) * np + c, v.v, d);
+            else ST::stT(P + (8 + i) * np + nb[i], v.v, d);
         }
     }
     if (OBS && (mode & OBS_STATS)) {
@@ -895,6 +930,100 @@ __global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kerne
         if (OBS && (mode & OBS_STATS)) {
             warp_block_reduce<double>(acc, red, sd.partials + (int64_t)te.y * NPART);
         }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Dataflow stepping: one cooperative launch advances a tile list by nsteps
+// time steps with no grid-wide barrier between steps.  Item (t, s) is tile t
+// at step s of the launch.  It reads and writes only slots of the cells of
+// tile t and of cells one link away, i.e. slots inside the 3 x 3 tile
+// neighbourhood of t, and those slots were last written by step s - 1 of the
+// same tiles (the AA pattern touches the same slot set of a cell on both
+// parities).  So the block waits until tile t and its eight neighbours (nbr,
+// -1 where there is no active tile) report step s - 1 complete, then updates
+// the tile and reports step s.
+//
+// Issue order.  The steps are taken in sweeps of sweep_steps (K) steps; one
+// sweep lists the items of its K steps in the order of a wavefront over the
+// tile rows ("bands"): at wavefront position j, band j at the sweep's step 0,
+// band j - L at step 1, ..., band j - (K-1) L at step K-1 (L >= 2 bands of
+// lag, fixed when the list is built).  Item q of the launch is entry
+// q mod per_sweep of the list, in sweep q / per_sweep; block b takes items b,
+// b + G, b + 2G, ... (G blocks, all co-resident).  Every item waited on comes
+// earlier in this order (a band's neighbours at the previous step sit L - 1
+// or more wavefront positions back, or in the previous sweep), and the
+// earliest unfinished item never waits, so the launch always completes.  With
+// K = 1 the order is step by step.  With K > 1 the slots a step writes are
+// read by the next step of the sweep a few bands later, while they are still
+// in L2, so DRAM sees about one read and one write per slot per sweep.  Every
+// wait is bounded: after FLOW_WAIT_LIMIT polls the block raises the launch's
+// abort word (which ends every other wait at once) and the sticky status word,
+// and the host reports the results as invalid instead of hanging.
+//
+// flags[0]: sticky status (non-zero after an expired wait; cleared by the
+//           host when it reports it);
+// flags[1]: abort word of the launch;
+// flags[2 + t]: steps of this launch that tile t has completed.
+// flags[1..] are zeroed before every launch.
+
+constexpr uint32_t FLOW_WAIT_LIMIT = 1u << 21;
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void flow_wait(const int* done, int target, int* flags) {
+    if (ld_acquire_gpu(done) >= target) return;
+    for (uint32_t it = 0; it < FLOW_WAIT_LIMIT; ++it) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(done) >= target) return;
+        if (*reinterpret_cast<volatile int*>(flags + 1)) return;
+    }
+    atomicExch(flags + 1, 1);
+    atomicExch(flags, 1);
+}
+
+template <class ST>
+__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
+    step_kernel_flow(const InstDesc* __restrict__ insts, const FlowArgs fa, Shape shape) {
+    __shared__ __align__(16) InstDesc sd;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    int* const done = fa.flags + 2;
+    int held = -1;  // instance whose descriptor sd holds (same in every thread)
+    const int64_t nsweeps = (fa.nsteps + fa.sweep_steps - 1) / fa.sweep_steps;
+    const int64_t total = nsweeps * fa.per_sweep;
+    for (int64_t q = blockIdx.x; q < total; q += gridDim.x) {
+        const int64_t w = q / fa.per_sweep;
+        const int4 it = fa.items[q - w * fa.per_sweep];
+        const int s = (int)w * fa.sweep_steps + (it.x >> 24);
+        if (s >= fa.nsteps) continue;  // the last sweep may be shorter
+        const int t = it.y;
+        const int4 te = make_int4(it.x & 0xFFFFFF, t, it.z, it.w);
+        if (s > 0 && tid < 9) {
+            const int u = tid == 0 ? t : fa.nbr[(int64_t)t * 8 + tid - 1];
+            if (u >= 0) flow_wait(done + u, s, fa.flags);
+        }
+        if (te.x != held) {  // sd is free: the previous item ended with a barrier
+            const uint64_t* src = reinterpret_cast<const uint64_t*>(insts + te.x);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&sd);
+            for (int k = tid; k < (int)(sizeof(InstDesc) / 8); k += nthreads) dst[k] = src[k];
+            held = te.x;
+        }
+        __syncthreads();
+        const int parity = (sd.parity ^ fa.flip ^ s) & 1;
+        double acc[NPART];
+        if (parity) tile_rows<ST, false, 1>(sd, te, 0, shape.rpt, acc);
+        else tile_rows<ST, false, 0>(sd, te, 0, shape.rpt, acc);
+        __syncthreads();
+        if (tid == 0) st_release_gpu(done + t, s + 1);
     }
 }
 

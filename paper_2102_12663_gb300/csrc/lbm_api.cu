@@ -31,6 +31,22 @@ cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles,
     void* args[] = {&insts, &tiles, &ntiles, &flip, &mode, &shape};
     return cudaLaunchKernel(pl.func, dim3(grid), pl.block, args, pl.smem, s);
 }
+
+StepPlan flow_plan(int precision, Shape shape, bool keep) {
+    return precision == 0 ? flow_plan_f64(shape, keep) : flow_plan_lp(precision, shape, keep);
+}
+
+// grid must not exceed the co-resident capacity (the cooperative launch checks it)
+cudaError_t launch_flow(int precision, const InstDesc* insts, const FlowArgs& fa, Shape shape,
+                        bool keep, int grid, cudaStream_t s) {
+    if (fa.ntiles <= 0 || fa.nsteps <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(fa.flags + 1, 0, (size_t)(fa.ntiles + 1) * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const StepPlan pl = flow_plan(precision, shape, keep);
+    FlowArgs a = fa;
+    void* args[] = {&insts, &a, &shape};
+    return cudaLaunchCooperativeKernel(pl.func, dim3(grid), pl.block, args, pl.smem, s);
+}
 }  // namespace lbm
 
 using namespace lbm;
@@ -76,7 +92,7 @@ static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct Layout {
     int64_t npad, max_tiles;
-    size_t desc, obs, mask, tiles, partials, usnap, pops, total;
+    size_t desc, obs, mask, tiles, nbr, flags, items, partials, usnap, pops, total;
 };
 
 static int64_t max_tiles_for(int nx, int ny) {
@@ -101,6 +117,9 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.obs = off; off = align_up(off + NOBS * sizeof(double));
     L.mask = off; off = align_up(off + (size_t)L.npad);
     L.tiles = off; off = align_up(off + (size_t)L.max_tiles * sizeof(int4));
+    L.nbr = off; off = align_up(off + (size_t)L.max_tiles * 8 * sizeof(int));
+    L.flags = off; off = align_up(off + (size_t)(L.max_tiles + 2) * sizeof(int));
+    L.items = off; off = align_up(off + (size_t)SWEEP_MAX * L.max_tiles * sizeof(int4));
     L.partials = off; off = align_up(off + (size_t)L.max_tiles * NPART * sizeof(double));
     L.usnap = off; off = align_up(off + 2 * (size_t)L.npad * real_size(prec));
     L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
@@ -122,9 +141,17 @@ struct lbm_domain {
     InstDesc* d_desc = nullptr;
     double* d_obs = nullptr;
     int4* d_tiles = nullptr;
+    int* d_nbr = nullptr;             // 8 neighbour tiles per tile (-1: none)
+    int* d_flags = nullptr;           // dataflow status, abort and progress words
+    int4* d_items = nullptr;          // work items of one dataflow sweep
+    int per_sweep = 0;                // items of one sweep
+    int sweep_k = 1;                  // steps per sweep in effect
+    bool periodic_x = false, periodic_y = false;
+    bool coop = false;                // device supports cooperative launches
+    int flow_grid = 0;                // co-resident blocks of the dataflow kernel
     int ntiles = 0;
     int64_t tiled_cells = 0;
-    lbm_launch launch{128, 1, 2, 0};
+    lbm_launch launch{128, 1, 2, 0, LBM_STEP_FLOW, 1, 0};
     lbm_params params{};
     bool have_params = false;
     int64_t step = 0;
@@ -146,8 +173,14 @@ static bool launch_ok(const lbm_launch& l) {
     return tw_ok && l.block_rows >= 1 && l.rows_per_thread >= 1 && l.rows_per_thread <= 64 &&
            l.tile_w * l.block_rows <= 256 &&
            (int64_t)l.tile_w * l.block_rows * l.rows_per_thread >= MIN_TILE_AREA &&
-           l.blocks_per_sm >= 0 && l.blocks_per_sm <= 32;
+           l.blocks_per_sm >= 0 && l.blocks_per_sm <= 32 &&
+           (l.stepping == LBM_STEP_FLOW || l.stepping == LBM_STEP_PER_LAUNCH) &&
+           l.sweep_steps >= 0 && l.sweep_steps <= SWEEP_MAX &&
+           (l.sweep_lag == 0 || (l.sweep_lag >= 2 && l.sweep_lag <= 4096));
 }
+
+// wavefront lag between consecutive steps of a sweep, in bands (tile rows)
+static constexpr int DEFAULT_SWEEP_LAG = 8;
 
 static Shape shape_of(const lbm_launch& l) { return Shape{l.tile_w, l.block_rows, l.rows_per_thread}; }
 
@@ -159,7 +192,9 @@ static int grid_of(const lbm_domain* d, int ntiles) {
 // tile list: every tw x th tile holding at least one active cell
 static lbm_status build_tiles(lbm_domain* d) {
     const int tw = d->launch.tile_w, th = d->launch.block_rows * d->launch.rows_per_thread;
+    const int ntx = (d->nx + tw - 1) / tw, nty = (d->ny + th - 1) / th;
     std::vector<int4> tiles;
+    std::vector<int> at((size_t)ntx * nty, -1);  // tile index of a tile-grid cell, -1 if none
     int64_t cells = 0;
     for (int y0 = 0; y0 < d->ny; y0 += th) {
         for (int x0 = 0; x0 < d->nx; x0 += tw) {
@@ -168,20 +203,73 @@ static lbm_status build_tiles(lbm_domain* d) {
                 for (int x = x0; x < std::min(d->nx, x0 + tw) && !any; ++x)
                     any = (d->hmask[(int64_t)y * d->nx + x] & TYPE_BITS) <= POROUS;
             if (any) {
+                at[(size_t)(y0 / th) * ntx + x0 / tw] = (int)tiles.size();
                 tiles.push_back(make_int4(0, (int)tiles.size(), x0, y0));
                 cells += (int64_t)std::min(tw, d->nx - x0) * std::min(th, d->ny - y0);
             }
         }
     }
     if ((int64_t)tiles.size() > d->L.max_tiles) return fail(LBM_EINVAL, "tile list overflow");
+    // neighbour tiles in the order of the links e_1..e_8, wrapping around
+    // periodic edges only (no active cell lies on a non-periodic edge, so no
+    // link crosses one)
+    static const int tdx[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+    static const int tdy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    std::vector<int> nbr(tiles.size() * 8);
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        const int tx = tiles[k].z / tw, ty = tiles[k].w / th;
+        for (int i = 0; i < 8; ++i) {
+            int ux = tx + tdx[i], uy = ty + tdy[i];
+            if (d->periodic_x) ux = (ux + ntx) % ntx;
+            if (d->periodic_y) uy = (uy + nty) % nty;
+            const bool in = ux >= 0 && ux < ntx && uy >= 0 && uy < nty;
+            nbr[k * 8 + i] = in ? at[(size_t)uy * ntx + ux] : -1;
+        }
+    }
+    // one sweep of K steps in wavefront order: position j holds band j at
+    // step 0, band j - L at step 1, ..., band j - (K-1) L at step K-1.  A
+    // y-periodic grid links the first and last bands, which no single
+    // wavefront orders, so it sweeps one step at a time.
+    int K = std::max(1, d->launch.sweep_steps);
+    if (d->periodic_y) K = 1;
+    const int Lg = d->launch.sweep_lag > 0 ? d->launch.sweep_lag : DEFAULT_SWEEP_LAG;
+    std::vector<int> band_start(nty + 1, 0);
+    for (const int4& t : tiles) band_start[t.w / th + 1] += 1;
+    for (int r = 0; r < nty; ++r) band_start[r + 1] += band_start[r];
+    std::vector<int4> items;
+    items.reserve((size_t)K * tiles.size());
+    for (int j = 0; j < nty + (K - 1) * Lg; ++j)
+        for (int k = 0; k < K; ++k) {
+            const int r = j - k * Lg;
+            if (r < 0 || r >= nty) continue;
+            for (int t = band_start[r]; t < band_start[r + 1]; ++t)
+                items.push_back(make_int4(k << 24, t, tiles[t].z, tiles[t].w));
+        }
+    d->sweep_k = K;
+    d->per_sweep = (int)items.size();
     d->ntiles = (int)tiles.size();
     d->tiled_cells = cells;
     d->h.ntiles = d->ntiles;
     d->htiles = tiles;
-    if (!tiles.empty())
+    if (!tiles.empty()) {
         CK(cudaMemcpyAsync(d->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, d->stream));
-    // pageable source: make sure the copy has consumed `tiles` before it dies
+        CK(cudaMemcpyAsync(d->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           d->stream));
+        CK(cudaMemcpyAsync(d->d_items, items.data(), items.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, d->stream));
+    }
+    // co-resident blocks of the dataflow kernel for this shape
+    d->flow_grid = 0;
+    if (d->coop) {
+        const StepPlan pl = flow_plan(d->prec, shape_of(d->launch), d->sweep_k > 1);
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.func,
+                                                         (int)(pl.block.x * pl.block.y), pl.smem));
+        if (d->launch.blocks_per_sm > 0) per_sm = std::min(per_sm, d->launch.blocks_per_sm);
+        d->flow_grid = per_sm * d->num_sms;
+    }
+    // pageable sources: make sure the copies have consumed them before they die
     CK(cudaStreamSynchronize(d->stream));
     return LBM_OK;
 }
@@ -348,10 +436,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(const InstDesc* __restric
         o[O_Q_IN] = a[P_Q_IN];
         o[O_Q_OUT] = a[P_Q_OUT];
         o[O_MASS] = a[P_MASS];
-        o[O_PEAK] = a[P_PEAK];
+        o[O_PEAK] = sqrt(a[P_PEAK]);  // the partials hold max |u|^2
         o[O_WSS_C] = a[P_N_C] > 0.0 ? a[P_WSS_C] / a[P_N_C] : 0.0;
         o[O_WSS_I] = a[P_N_I] > 0.0 ? a[P_WSS_I] / a[P_N_I] : 0.0;
-        o[O_RESID] = d.snap_valid ? a[P_RESID] : -1.0;
+        o[O_RESID] = d.snap_valid ? sqrt(a[P_RESID]) : -1.0;
         o[O_N_FLUID] = a[P_N_FLUID];
         o[O_N_C] = a[P_N_C];
         o[O_N_I] = a[P_N_I];
@@ -438,6 +526,14 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     d->d_desc = reinterpret_cast<InstDesc*>(d->base + d->L.desc);
     d->d_obs = reinterpret_cast<double*>(d->base + d->L.obs);
     d->d_tiles = reinterpret_cast<int4*>(d->base + d->L.tiles);
+    d->d_nbr = reinterpret_cast<int*>(d->base + d->L.nbr);
+    d->d_flags = reinterpret_cast<int*>(d->base + d->L.flags);
+    d->d_items = reinterpret_cast<int4*>(d->base + d->L.items);
+    d->periodic_x = desc->kind == LBM_GEOM_MASK && desc->periodic_x != 0;
+    d->periodic_y = desc->kind == LBM_GEOM_MASK && desc->periodic_y != 0;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess)
+        d->coop = coop != 0;
     InstDesc& h = d->h;
     std::memset(&h, 0, sizeof(h));
     h.pops = d->base + d->L.pops;
@@ -465,6 +561,11 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     if (ce != cudaSuccess) {
         delete d;
         return fail(LBM_ECUDA, "mask upload failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream);
+    if (ce != cudaSuccess) {
+        delete d;
+        return fail(LBM_ECUDA, "status word reset failed: %s", cudaGetErrorString(ce));
     }
     if ((st = build_tiles(d)) != LBM_OK || (st = upload_desc(d)) != LBM_OK) {
         delete d;
@@ -648,6 +749,20 @@ extern "C" lbm_status lbm_step(lbm_domain* d, int64_t nsteps) {
     if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
     int64_t k = 0;
     lbm_status st;
+    if (d->launch.stepping == LBM_STEP_FLOW && d->flow_grid > 0 && nsteps >= 1 && d->ntiles > 0) {
+        // one dataflow launch per chunk of at most INT32_MAX / ntiles steps
+        const int64_t chunk = std::max<int64_t>(1, (int64_t)INT32_MAX / d->ntiles - 1);
+        while (k < nsteps) {
+            const int n = (int)std::min<int64_t>(nsteps - k, chunk);
+            FlowArgs fa{d->d_items, d->d_nbr, d->d_flags, d->ntiles, d->per_sweep, d->sweep_k, n,
+                        (int)(d->step & 1)};
+            CK(launch_flow(d->prec, d->d_desc, fa, shape_of(d->launch), d->sweep_k > 1,
+                           d->flow_grid, d->stream));
+            d->step += n;
+            k += n;
+        }
+        return LBM_OK;
+    }
     if (nsteps >= GRAPH_STEPS + 1 && d->ntiles > 0) {
         if (d->step & 1) {
             if ((st = step_once(d, 0)) != LBM_OK) return st;
@@ -672,11 +787,23 @@ static lbm_status check_step_status() {
     return LBM_OK;
 }
 
+// Reads and clears the sticky status word of the domain's dataflow launches.
+static lbm_status check_flow_status(lbm_domain* d) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, d->d_flags, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    if (st == 0) return LBM_OK;
+    CK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream));
+    return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
+}
+
 static lbm_status fetch_obs(lbm_domain* d, double* o) {
     CK(launch_finalize(d->d_desc, 1, d->stream));
     CK(cudaMemcpyAsync(o, d->d_obs, NOBS * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
     CK(cudaStreamSynchronize(d->stream));
-    return check_step_status();
+    lbm_status st = check_step_status();
+    if (st != LBM_OK) return st;
+    return check_flow_status(d);
 }
 
 static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out) {
@@ -917,7 +1044,7 @@ struct lbm_batch {
     std::vector<lbm_domain*> members;  // table order
     std::vector<InstDesc> htable;
     std::vector<double> hobs;
-    lbm_launch launch{128, 1, 2, 0};
+    lbm_launch launch{128, 1, 2, 0, LBM_STEP_FLOW, 1, 0};
     int ntiles = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;

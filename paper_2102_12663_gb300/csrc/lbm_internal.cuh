@@ -24,7 +24,8 @@ enum : int {
     OBS_WRITE = 8   // also perform the step (else observe only)
 };
 
-// Per-tile partial slots (FP64).
+// Per-tile partial slots (FP64).  P_PEAK and P_RESID hold the maxima of the
+// squared norms; the fold takes their square roots.
 enum : int {
     P_SUM_P = 0, P_N_FLUID, P_MASS, P_Q_IN, P_Q_OUT, P_WSS_C, P_N_C, P_WSS_I, P_N_I,
     P_NAN, P_PEAK, P_RESID, NPART
@@ -95,30 +96,45 @@ struct Shape {
 __host__ __device__ constexpr int cells_per_thread(int precision) { return precision == 0 ? 1 : 2; }
 
 // ---- storage traits --------------------------------------------------------
-struct StF64 {
+// Store cache policy of a storage trait.  ST_STREAM: evict-first streaming
+// stores (with one step per pass over the grid, the next step reads the slot
+// back from DRAM anyway).  ST_KEEP: ordinary L2 stores (a sweep of several
+// steps reads the slot back while it is still in L2).
+enum : int { ST_STREAM = 0, ST_KEEP = 1 };
+template <int POL, class V>
+__device__ __forceinline__ void st_pol(V* p, V v) {
+    if constexpr (POL == ST_STREAM) __stcs(p, v);
+    else __stcg(p, v);
+}
+
+// Populations are read through L2 only: each slot is read once per step, and
+// the dataflow kernel reads slots that other SMs wrote during the same launch.
+template <int POL = ST_STREAM>
+struct StF64T {
     using T = double;
     using R = double;
-    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return *p; }
-    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { *p = v; }
-    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return *p; }
-    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { *p = v; }
+    static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
 };
 // The FP32-arithmetic storages read populations through L2 only (each slot
 // is read once per step, so L1 would only hold dead lines) and write them as
 // streaming stores (evict-first: the next step reads them from DRAM anyway).
-struct StF32 {
+template <int POL = ST_STREAM>
+struct StF32T {
     using T = float;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
-    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { __stcs(p, v); }
+    static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
-    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { __stcs(p, v); }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     // two neighbouring cells (p 8-byte aligned)
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc&) {
         return __ldcg(reinterpret_cast<const float2*>(p));
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc&) {
-        __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
+        st_pol<POL>(reinterpret_cast<float2*>(p), make_float2(a, b));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) { return ldf2(p, d); }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) { stf2(p, a, b, d); }
@@ -126,34 +142,35 @@ struct StF32 {
     static __device__ __forceinline__ R sldf(const T* p, const InstDesc&) { return *p; }
     static __device__ __forceinline__ R sldT(const T* p, const InstDesc&) { return *p; }
 };
-struct StF16 {
+template <int POL = ST_STREAM>
+struct StF16T {
     using T = __half;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __half2float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        __stcs(p, __float2half_rn(v * d.fscale));
+        st_pol<POL>(p, __float2half_rn(v * d.fscale));
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
         return __half2float(__ldcg(p)) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        __stcs(p, __float2half_rn((v - d.Tshift) * d.fscale));
+        st_pol<POL>(p, __float2half_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
         const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
         return make_float2(v.x * d.finv, v.y * d.finv);
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
-        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(a * d.fscale, b * d.fscale));
+        st_pol<POL>(reinterpret_cast<__half2*>(p), __floats2half2_rn(a * d.fscale, b * d.fscale));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
         const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
         return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
     }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        __stcs(reinterpret_cast<__half2*>(p),
+        st_pol<POL>(reinterpret_cast<__half2*>(p),
                __floats2half2_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) { return __half2float(*p) * d.finv; }
@@ -161,34 +178,35 @@ struct StF16 {
         return __half2float(*p) * d.finv + d.Tshift;
     }
 };
-struct StBF16 {
+template <int POL = ST_STREAM>
+struct StBF16T {
     using T = __nv_bfloat16;
     using R = float;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __bfloat162float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
-        __stcs(p, __float2bfloat16_rn(v * d.fscale));
+        st_pol<POL>(p, __float2bfloat16_rn(v * d.fscale));
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
         return __bfloat162float(__ldcg(p)) * d.finv + d.Tshift;
     }
     static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        __stcs(p, __float2bfloat16_rn((v - d.Tshift) * d.fscale));
+        st_pol<POL>(p, __float2bfloat16_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
         const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
         return make_float2(v.x * d.finv, v.y * d.finv);
     }
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
-        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a * d.fscale, b * d.fscale));
+        st_pol<POL>(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a * d.fscale, b * d.fscale));
     }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
         const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
         return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
     }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        __stcs(reinterpret_cast<__nv_bfloat162*>(p),
+        st_pol<POL>(reinterpret_cast<__nv_bfloat162*>(p),
                __floats2bfloat162_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) {
@@ -198,6 +216,11 @@ struct StBF16 {
         return __bfloat162float(*p) * d.finv + d.Tshift;
     }
 };
+
+using StF64 = StF64T<ST_STREAM>;
+using StF32 = StF32T<ST_STREAM>;
+using StF16 = StF16T<ST_STREAM>;
+using StBF16 = StBF16T<ST_STREAM>;
 
 // ---- launchers (one translation unit per arithmetic precision) -----------
 // precision: 0 f64, 1 f32, 2 f16-dev, 3 bf16-dev.
@@ -218,5 +241,22 @@ StepPlan step_plan(int precision, bool obs, Shape shape);
 cudaError_t take_step_status(int* status);
 StepPlan step_plan_f64(bool obs, Shape shape);
 StepPlan step_plan_lp(int precision, bool obs, Shape shape);
+// Dataflow kernel advancing a tile list by many steps in one cooperative
+// launch; keep = L2-resident stores (sweeps of several steps).
+StepPlan flow_plan(int precision, Shape shape, bool keep);
+StepPlan flow_plan_f64(Shape shape, bool keep);
+StepPlan flow_plan_lp(int precision, Shape shape, bool keep);
+
+// Work items of a dataflow sweep: x = (k << 24) | instance (k: step of the
+// sweep), y = tile index in the tile list, z, w = tile origin.
+constexpr int SWEEP_MAX = 8;
+struct FlowArgs {
+    const int4* items;  // per_sweep items of one sweep, in issue order
+    const int* nbr;     // 8 neighbour tiles per tile, -1: none
+    int* flags;         // status, abort, then one progress word per tile
+    int ntiles, per_sweep, sweep_steps, nsteps, flip;
+};
+cudaError_t launch_flow(int precision, const InstDesc* insts, const FlowArgs& fa, Shape shape,
+                        bool keep, int grid, cudaStream_t s);
 
 }  // namespace lbm

@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(256) noalloc_fold_kernel(const InstDesc* __res
         o[O_Q_IN] = a[P_Q_IN];
         o[O_Q_OUT] = a[P_Q_OUT];
         o[O_MASS] = a[P_MASS];
-        o[O_PEAK] = a[P_PEAK];
+        o[O_PEAK] = sqrt(a[P_PEAK]);  // the partials hold max |u|^2
         o[O_WSS_C] = a[P_N_C] > 0.0 ? a[P_WSS_C] / a[P_N_C] : 0.0;
         o[O_WSS_I] = a[P_N_I] > 0.0 ? a[P_WSS_I] / a[P_N_I] : 0.0;
-        o[O_RESID] = insts->snap_valid ? a[P_RESID] : -1.0;
+        o[O_RESID] = insts->snap_valid ? sqrt(a[P_RESID]) : -1.0;
         o[O_N_FLUID] = a[P_N_FLUID];
         o[O_N_C] = a[P_N_C];
         o[O_N_I] = a[P_N_I];

@@ -14,4 +14,13 @@ StepPlan step_plan_f64(bool obs, Shape shape) {
     return p;
 }
 
+StepPlan flow_plan_f64(Shape shape, bool keep) {
+    StepPlan p;
+    p.func = keep ? reinterpret_cast<const void*>(&step_kernel_flow<StF64T<ST_KEEP>>)
+                  : reinterpret_cast<const void*>(&step_kernel_flow<StF64>);
+    p.block = dim3(shape.tw, shape.bh);
+    p.smem = 0;
+    return p;
+}
+
 }  // namespace lbm

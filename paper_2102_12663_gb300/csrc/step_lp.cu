@@ -38,6 +38,23 @@ StepPlan step_plan_lp(int precision, bool obs, Shape shape) {
     }
 }
 
+template <class ST>
+static StepPlan flow_t(Shape shape) {
+    StepPlan p;
+    p.func = reinterpret_cast<const void*>(&step_kernel_flow<ST>);
+    p.block = dim3(shape.tw / cells_per_thread(1), shape.bh);
+    p.smem = 0;
+    return p;
+}
+
+StepPlan flow_plan_lp(int precision, Shape shape, bool keep) {
+    switch (precision) {
+    case 1: return keep ? flow_t<StF32T<ST_KEEP>>(shape) : flow_t<StF32>(shape);
+    case 2: return keep ? flow_t<StF16T<ST_KEEP>>(shape) : flow_t<StF16>(shape);
+    default: return keep ? flow_t<StBF16T<ST_KEEP>>(shape) : flow_t<StBF16>(shape);
+    }
+}
+
 }  // namespace lbm
 
 namespace lbm {

@@ -83,9 +83,16 @@ class Observables(ctypes.Structure):
     ]
 
 
+# lbm_launch.stepping
+STEP_FLOW = 0          # one cooperative dataflow launch for many steps
+STEP_PER_LAUNCH = 1    # one launch per step (CUDA-graph replay)
+
+
 class Launch(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("block_rows", ctypes.c_int32),
-                ("rows_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("rows_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("stepping", ctypes.c_int32), ("sweep_steps", ctypes.c_int32),
+                ("sweep_lag", ctypes.c_int32)]
 
 
 _lib = None
@@ -358,9 +365,11 @@ class Domain:
         check(self._L.lbm_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
 
     # -- launch shape and introspection -----------------------------------
-    def set_launch(self, tile_w=128, block_rows=2, rows_per_thread=1, blocks_per_sm=0):
+    def set_launch(self, tile_w=128, block_rows=2, rows_per_thread=1, blocks_per_sm=0,
+                   stepping=STEP_FLOW, sweep_steps=1, sweep_lag=0):
         check(self._L.lbm_set_launch(self._h, ctypes.byref(
-            Launch(tile_w, block_rows, rows_per_thread, blocks_per_sm))))
+            Launch(tile_w, block_rows, rows_per_thread, blocks_per_sm, stepping, sweep_steps,
+                   sweep_lag))))
 
     def get_launch(self) -> dict:
         l = Launch()

@@ -44,8 +44,9 @@ def test_struct_layout_matches_header(tmp_path):
     fields = [("lbm_params", "seed"), ("lbm_params", "p_sc_pa"), ("lbm_observables", "nan_flag"),
               ("lbm_geometry_desc", "chamber_angle_deg"), ("lbm_geometry_desc", "host_mask"),
               ("lbm_geometry_info", "arc_xc"), ("lbm_params", "h_tm"),
-              ("lbm_observables", "u_seep")]
+              ("lbm_observables", "u_seep"), ("lbm_launch", "stepping"), ("lbm_launch", "sweep_lag")]
     body += "".join(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));' for s, f in fields)
+    body += 'printf("STEP_FLOW %d\\n", LBM_STEP_FLOW);printf("STEP_PER_LAUNCH %d\\n", LBM_STEP_PER_LAUNCH);'
     c = tmp_path / "probe.c"
     c.write_text(f'#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){{{body}return 0;}}\n')
     exe = tmp_path / "probe"
@@ -56,6 +57,8 @@ def test_struct_layout_matches_header(tmp_path):
         assert int(out[k]) == ctypes.sizeof(cls), k
     for s, f in fields:
         assert int(out[f"{s}.{f}"]) == getattr(structs[s], f).offset, f"{s}.{f}"
+    assert int(out["STEP_FLOW"]) == lbm.STEP_FLOW
+    assert int(out["STEP_PER_LAUNCH"]) == lbm.STEP_PER_LAUNCH
 
 
 @pytest.mark.parametrize("nx,ny,angle", [(160, 80, 45.0), (320, 160, 20.0), (512, 256, 33.3),
@@ -92,6 +95,9 @@ def test_domain_bytes_and_no_gpu_needed_for_sizes(L):
     b16 = L.lbm_domain_bytes(ctypes.byref(g), lbm.F16DEV)
     b64 = L.lbm_domain_bytes(ctypes.byref(g), lbm.F64)
     N = 4096 * 2048
-    assert 13 * 4 * N < b32 < 13 * 4 * N * 1.2
+    # populations (13 x 4 B), velocity snapshot (2 x 4 B) and mask (1 B) per
+    # cell, plus per-tile tables (tile list, partials, neighbour lists,
+    # progress words, sweep items)
+    assert 61 * N < b32 < 61 * N + (32 << 20)
     assert b16 < b32 < b64
     assert L.lbm_domain_bytes(ctypes.byref(g), 7) == 0

@@ -111,10 +111,11 @@ def test_eye_fp64_full_config_5000_steps():
     dict(tile_w=256, block_rows=1, rows_per_thread=1, blocks_per_sm=2),
     dict(tile_w=128, block_rows=2, rows_per_thread=4, blocks_per_sm=1),
 ])
-def test_ragged_grid_and_launch_shapes(launch):
+@pytest.mark.parametrize("stepping", [lbm.STEP_FLOW, lbm.STEP_PER_LAUNCH])
+def test_ragged_grid_and_launch_shapes(launch, stepping):
     """A grid that is no multiple of any tile (150 x 75, 33 degrees) under
-    several tile shapes and persistent grids."""
-    dom, ref, _ = eye_pair(150, 75, "f64", angle=33.0, launch=launch)
+    several tile shapes and grid sizes, with dataflow and per-step launches."""
+    dom, ref, _ = eye_pair(150, 75, "f64", angle=33.0, launch=dict(launch, stepping=stepping))
     dom.step(37)
     ref.run(37)
     assert rel_err(dom, ref) <= TOL["f64"]
@@ -151,9 +152,12 @@ def test_periodic_channel_and_porous_box():
     dict(tile_w=64, block_rows=1, rows_per_thread=16, blocks_per_sm=0),
     dict(tile_w=128, block_rows=1, rows_per_thread=5, blocks_per_sm=1),
 ])
-def test_periodic_wrap_low_precision(prec, launch):
+@pytest.mark.parametrize("stepping", [lbm.STEP_FLOW, lbm.STEP_PER_LAUNCH])
+def test_periodic_wrap_low_precision(prec, launch, stepping):
     """Wrap-around columns and rows on the FP32-arithmetic paths (pairs at a
-    periodic edge, strips that wrap in y), against the FP64 oracle."""
+    periodic edge, strips that wrap in y; one launch per step takes the
+    staged kernel for these one-row shapes), against the FP64 oracle."""
+    launch = dict(launch, stepping=stepping)
     m, d = W.porous_box(64, 24)
     m[5:9, 20:30] = 1
     m[12:14, :] = 0  # a fluid lane across the periodic box
