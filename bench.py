@@ -341,7 +341,8 @@ def run_gpu(args):
     return 0
 
 
-LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=0)
+LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0, sweep_steps=1,
+              sweep_lag=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):

@@ -610,15 +610,23 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
     if constexpr (V == 2) {
         // the pair path needs whole warps on one row and even rows
         const bool vec_ok = !OBS && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0;
+        // a pure tile (every cell fluid, in the grid, away from boundaries)
+        // takes the pair path without reading its mask
+        const bool pure = (te.y & TILE_PURE) != 0;
         for (int r = 0; r < rpt; ++r) {
             const int y = te.w + threadIdx.y + r * blockDim.y;
             bool fast = false;
             if (vec_ok) {
-                const bool in = y < sd.ny && x + 1 < sd.nx;
-                const uint32_t m2 =
-                    in ? *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x) : 0xFFFFu;
-                // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
-                fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+                uint32_t m2 = 0u;
+                if (pure) {
+                    fast = true;
+                } else {
+                    const bool in = y < sd.ny && x + 1 < sd.nx;
+                    if (in) m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x);
+                    else m2 = 0xFFFFu;
+                    // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
+                    fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+                }
                 if (fast)
                     update_pair_interior<ST, PAR>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
                                                   (m2 & 0x100u) != 0 && sd.tm_model == 0);
@@ -928,7 +936,7 @@ __global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kerne
         if (parity) tile_rows<ST, OBS, 1>(sd, te, mode, shape.rpt, acc);
         else tile_rows<ST, OBS, 0>(sd, te, mode, shape.rpt, acc);
         if (OBS && (mode & OBS_STATS)) {
-            warp_block_reduce<double>(acc, red, sd.partials + (int64_t)te.y * NPART);
+            warp_block_reduce<double>(acc, red, sd.partials + (int64_t)(te.y & TILE_INDEX) * NPART);
         }
     }
 }
@@ -1005,8 +1013,8 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
         const int4 it = fa.items[q - w * fa.per_sweep];
         const int s = (int)w * fa.sweep_steps + (it.x >> 24);
         if (s >= fa.nsteps) continue;  // the last sweep may be shorter
-        const int t = it.y;
-        const int4 te = make_int4(it.x & 0xFFFFFF, t, it.z, it.w);
+        const int t = it.y & TILE_INDEX;
+        const int4 te = make_int4(it.x & 0xFFFFFF, it.y, it.z, it.w);
         if (s > 0 && tid < 9) {
             const int u = tid == 0 ? t : fa.nbr[(int64_t)t * 8 + tid - 1];
             if (u >= 0) flow_wait(done + u, s, fa.flags);

@@ -203,8 +203,13 @@ static lbm_status build_tiles(lbm_domain* d) {
                 for (int x = x0; x < std::min(d->nx, x0 + tw) && !any; ++x)
                     any = (d->hmask[(int64_t)y * d->nx + x] & TYPE_BITS) <= POROUS;
             if (any) {
+                // pure: wholly inside the grid, fluid only, no cell linked to a boundary
+                bool pure = x0 + tw <= d->nx && y0 + th <= d->ny;
+                for (int y = y0; y < std::min(d->ny, y0 + th) && pure; ++y)
+                    for (int x = x0; x < std::min(d->nx, x0 + tw) && pure; ++x)
+                        pure = d->hmask[(int64_t)y * d->nx + x] == FLUID;
                 at[(size_t)(y0 / th) * ntx + x0 / tw] = (int)tiles.size();
-                tiles.push_back(make_int4(0, (int)tiles.size(), x0, y0));
+                tiles.push_back(make_int4(0, (int)tiles.size() | (pure ? TILE_PURE : 0), x0, y0));
                 cells += (int64_t)std::min(tw, d->nx - x0) * std::min(th, d->ny - y0);
             }
         }
@@ -243,7 +248,7 @@ static lbm_status build_tiles(lbm_domain* d) {
             const int r = j - k * Lg;
             if (r < 0 || r >= nty) continue;
             for (int t = band_start[r]; t < band_start[r + 1]; ++t)
-                items.push_back(make_int4(k << 24, t, tiles[t].z, tiles[t].w));
+                items.push_back(make_int4(k << 24, tiles[t].y, tiles[t].z, tiles[t].w));
         }
     d->sweep_k = K;
     d->per_sweep = (int)items.size();

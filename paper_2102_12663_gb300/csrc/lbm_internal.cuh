@@ -87,6 +87,13 @@ __host__ __device__ __forceinline__ const Phys<double>& phys<double>(const InstD
 template <>
 __host__ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDesc& d) { return d.pf; }
 
+// Tile list entries are int4 {instance, local tile | TILE_PURE, x0, y0}.
+// TILE_PURE marks a tile that lies wholly inside the grid and holds only
+// fluid cells none of which links to a boundary: the FP32-arithmetic kernels
+// update it by the pair path without reading its mask.
+constexpr int TILE_PURE = 1 << 30;
+constexpr int TILE_INDEX = TILE_PURE - 1;
+
 struct Shape {
     int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = (tw / V) x bh threads
 };
@@ -248,7 +255,7 @@ StepPlan flow_plan_f64(Shape shape, bool keep);
 StepPlan flow_plan_lp(int precision, Shape shape, bool keep);
 
 // Work items of a dataflow sweep: x = (k << 24) | instance (k: step of the
-// sweep), y = tile index in the tile list, z, w = tile origin.
+// sweep), y = tile index in the tile list (| TILE_PURE), z, w = tile origin.
 constexpr int SWEEP_MAX = 8;
 struct FlowArgs {
     const int4* items;  // per_sweep items of one sweep, in issue order
