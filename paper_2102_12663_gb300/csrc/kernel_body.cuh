@@ -1005,6 +1005,7 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
     int* const done = fa.flags + 2;
+    const int rel = nthreads > 32 ? 32 : 0;
     int held = -1;  // instance whose descriptor sd holds (same in every thread)
     const int64_t nsweeps = (fa.nsteps + fa.sweep_steps - 1) / fa.sweep_steps;
     const int64_t total = nsweeps * fa.per_sweep;
@@ -1031,7 +1032,9 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
         if (parity) tile_rows<ST, false, 1>(sd, te, 0, shape.rpt, acc);
         else tile_rows<ST, false, 0>(sd, te, 0, shape.rpt, acc);
         __syncthreads();
-        if (tid == 0) st_release_gpu(done + t, s + 1);
+        // a thread outside warp 0 reports, so that the release overlaps warp
+        // 0's polls for the next item
+        if (tid == rel) st_release_gpu(done + t, s + 1);
     }
 }
 
