@@ -65,6 +65,14 @@ class Obs(ctypes.Structure):
         "residual", "n_fluid", "n_cornea", "n_iris")]
 
 
+class VortexOut(ctypes.Structure):
+    _fields_ = [("intensity", ctypes.c_double), ("intensity_abs", ctypes.c_double),
+                ("psi_max", ctypes.c_double), ("psi_min", ctypes.c_double),
+                ("max_x", ctypes.c_int32), ("max_y", ctypes.c_int32),
+                ("min_x", ctypes.c_int32), ("min_y", ctypes.c_int32),
+                ("n_fluid", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liblbm_oracle.so (gcc, -O2,
     -ffp-contract=off, OpenMP over rows)."""
@@ -107,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.orc_seepage_velocity.restype = ctypes.c_double
         L.orc_seepage_velocity.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double]
         L.orc_set_threads.argtypes = [ctypes.c_int32]
+        L.orc_vortex.argtypes = [ctypes.POINTER(Geom), u8p, dp, ctypes.POINTER(VortexOut)]
         L.orc_get_threads.restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -184,6 +193,16 @@ def mask_geom(nx: int, ny: int, periodic_x: int = 0, periodic_y: int = 0,
 def seepage_velocity(params: Params, iop: float, h_tm: float) -> float:
     """Lumped TM (Sec. 2.3): seepage speed for the current IOP."""
     return float(lib().orc_seepage_velocity(ctypes.byref(params), float(iop), float(h_tm)))
+
+
+def vortex(geom: Geom, mask: np.ndarray, u: np.ndarray) -> dict:
+    """Vortex measures (Eq. 18, Tab. 3) of the velocity field u[2, ny, nx]."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    uu = np.ascontiguousarray(u, dtype=np.float64).reshape(2, -1)
+    assert m.size == geom.nx * geom.ny == uu.shape[1]
+    o = VortexOut()
+    lib().orc_vortex(ctypes.byref(geom), _u8(m), _dp(uu), ctypes.byref(o))
+    return {k: getattr(o, k) for k, _ in VortexOut._fields_}
 
 
 def feq(p: float, ux: float, uy: float) -> np.ndarray:

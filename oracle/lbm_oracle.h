@@ -78,6 +78,17 @@ void orc_observe(const orc_geom* G, const orc_params* P, const uint8_t* type,
                  const double* f, const double* T, const double* u_snap,
                  orc_obs* obs);
 double orc_seepage_velocity(const orc_params* P, double iop, double h_tm);
+
+/* Vortex measures of a velocity field (Eq. 18, Tab. 3).  u holds u_x in
+ * u[0..N) and u_y in u[N..2N) (values at non-active cells are ignored). */
+typedef struct {
+    double intensity;      /* sum over fluid cells of 2 omega_z (cell area 1) */
+    double intensity_abs;  /* sum over fluid cells of 2 |omega_z| */
+    double psi_max, psi_min;         /* extrema of the stream function over fluid cells */
+    int32_t max_x, max_y, min_x, min_y;
+    double n_fluid;
+} orc_vortex_out;
+void orc_vortex(const orc_geom* G, const uint8_t* type, const double* u, orc_vortex_out* out);
 void orc_fields(const orc_geom* G, const uint8_t* type, const double* f,
                 const double* T, double* u, double* p, double* Tf);
 void orc_run(const orc_geom* G, const orc_params* P, const uint8_t* type,

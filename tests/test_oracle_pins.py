@@ -354,3 +354,59 @@ def test_lumped_tm_steady_state_obeys_darcy_law():
     assert o["iop"] == pytest.approx(nu * h * u / K, rel=1e-8)
     assert P.u_seep == pytest.approx(u, rel=1e-8)
     assert qo == pytest.approx(qi, rel=1e-8)
+
+
+# ---- vortex measures (Eq. 18, Tab. 3) ----------------------------------------
+
+def test_vortex_taylor_green_closed_forms():
+    """Taylor-Green field u_x = U sin(kx) cos(ky), u_y = -U cos(kx) sin(ky) on a
+    fully periodic box.  The centred differences of the trigonometric field are
+    exact multiples of it: 2 omega_z = 2 U sin(k) sin(kx) sin(ky), so the
+    signed sum over whole periods is zero and the sum of |2 omega_z| factors
+    into (sum_x |sin kx|)^2.  The midpoint sum of u_x along y is
+    U sin(kx) (cot(k/2) sin(ky) + 1) / 2, largest at (n/4, n/4) and smallest
+    at (3n/4, n/4)."""
+    n, U = 32, 1e-3
+    k = 2 * math.pi / n
+    x = np.arange(n)
+    X, Y = np.meshgrid(x, x)  # [y, x]
+    u = np.stack([U * np.sin(k * X) * np.cos(k * Y), -U * np.cos(k * X) * np.sin(k * Y)])
+    m, d = W.porous_box(n, n)
+    m[:] = O.FLUID
+    g = O.mask_geom(n, n, 1, 1)
+    v = O.vortex(g, m, u)
+    s1 = np.abs(np.sin(k * x)).sum()
+    assert v["n_fluid"] == n * n
+    assert abs(v["intensity"]) <= 1e-15 * n * n * U
+    assert v["intensity_abs"] == pytest.approx(2 * U * math.sin(k) * s1 * s1, rel=1e-12)
+    peak = U * (1 / math.tan(k / 2) + 1) / 2
+    assert v["psi_max"] == pytest.approx(peak, rel=1e-12)
+    assert (v["max_x"], v["max_y"]) == (n // 4, n // 4)
+    assert v["psi_min"] == pytest.approx(-peak, rel=1e-12)
+    assert (v["min_x"], v["min_y"]) == (3 * n // 4, n // 4)
+
+
+def test_vortex_poiseuille_wall_stencil_and_ties():
+    """Plane Poiseuille u_x = G Y (H - Y), Y = y - 1/2, between halfway walls
+    (fluid rows 1..H, periodic in x).  Interior rows see the exact slope
+    G (H - 2Y); a wall row sees the wall value 0 at distance 1/2, which gives
+    the one-sided slope +-G (H - 3/2).  The signed sum vanishes by symmetry.
+    psi grows with y in every column, so its extrema are ties across x that go
+    to x = 0."""
+    H, nx, G = 20, 6, 1e-5
+    m, d = W.channel(nx, H)
+    g = O.mask_geom(nx, H + 2, 1, 0)
+    y = np.arange(H + 2, dtype=float)
+    Yc = y - 0.5
+    prof = np.where((y >= 1) & (y <= H), G * Yc * (H - Yc), 0.0)
+    u = np.zeros((2, H + 2, nx))
+    u[0] = prof[:, None]
+    v = O.vortex(g, m, u)
+    slope = [G * (H - 1.5)] + [G * (H - 2 * (j - 0.5)) for j in range(2, H)] + [-G * (H - 1.5)]
+    assert v["intensity"] == pytest.approx(0.0, abs=1e-15 * nx * H * G * H)
+    assert v["intensity_abs"] == pytest.approx(nx * sum(abs(s) for s in slope), rel=1e-12)
+    top = sum(prof[1:H]) + 0.5 * prof[H]
+    assert v["psi_max"] == pytest.approx(top, rel=1e-14)
+    assert (v["max_x"], v["max_y"]) == (0, H)
+    assert v["psi_min"] == pytest.approx(0.5 * prof[1], rel=1e-14)
+    assert (v["min_x"], v["min_y"]) == (0, 1)
