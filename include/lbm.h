@@ -294,6 +294,38 @@ double lbm_step_bytes(const lbm_domain* dom);
 
 void lbm_destroy_domain(lbm_domain* dom);
 
+/* ---- vortex measures (Eq. 18, Tab. 3) -------------------------------------
+ * Vortex intensity I = 2 * integral over the chamber of the vorticity
+ * omega_z = (1/2)(du_y/dx - du_x/dy), taken over the fluid cells (cell area
+ * 1 in lattice units), and the vortex centres, read as the extrema of the
+ * stream function psi (u_x = dpsi/dy).  The signed integral over a closed
+ * no-slip chamber is a boundary circulation and nearly vanishes (Stokes'
+ * theorem), so the integral of |omega_z| is returned beside it; Tab. 3's
+ * growth of I with the temperature difference fits the latter.
+ * Derivatives: centred differences of the axis neighbours; a neighbour that
+ * is not fluid or porous contributes the no-slip value 0 at half a link.
+ * psi: the midpoint sum of u_x up each column from y = 0.  Extrema ties go to
+ * the lowest flat index y*nx + x. */
+typedef struct lbm_vortex_info {
+    double intensity;           /* sum of 2 omega_z over fluid cells, lattice units */
+    double intensity_abs;       /* sum of 2 |omega_z| */
+    double intensity_phys;      /* intensity x dx^2/dt in m^2/s (0 without dx_m, dt_s) */
+    double intensity_abs_phys;
+    double psi_max, psi_min;    /* stream-function extrema over fluid cells, lattice units */
+    int32_t max_x, max_y;       /* cell of psi_max (-1 without fluid cells) */
+    int32_t min_x, min_y;       /* cell of psi_min */
+    double max_mm[2], min_mm[2];/* those cell centres in mm, ((x + 1/2) dx, (y + 1/2) dx) */
+    int64_t n_fluid;
+} lbm_vortex_info;
+
+/* Vortex measures of the device velocity field dev_u (FP64, 2 x ny x nx: u_x
+ * then u_y, the layout lbm_read_field writes; values at non-active cells are
+ * ignored) on this domain's grid and mask.  Uses the domain's partials region
+ * as scratch and synchronises the domain's stream.  EINVAL for a null
+ * argument or a one-row grid of at most 32 cells (too small a partials
+ * region). */
+lbm_status lbm_vortex(lbm_domain* dom, const double* dev_u, lbm_vortex_info* out);
+
 /* ---- batches: many problems, one launch per time step --------------------
  * A batch advances many domains of one storage precision, of any sizes and
  * parameters, with a single launch of the fused step per time step over the

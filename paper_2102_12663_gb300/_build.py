@@ -1,12 +1,13 @@
 """In-tree build of the CUDA library ``_build/liblbm.so`` for sm_103a.
 
-Five translation units compiled in parallel with nvcc, linked against the
+Six translation units compiled in parallel with nvcc, linked against the
 shared CUDA runtime (the same one PyTorch loads):
   lbm_api.cu    C ABI, initial state, read-back, finalisation (-fmad=false)
   step_f64.cu   FP64 fused step (-fmad=false: no contracted multiply-adds)
   step_lp.cu    FP32-arithmetic fused steps (FP32, FP16 and BF16 storage)
   geometry.cpp  host-side eye builder and mask validation
   noalloc.cu    observables with library-held device scratch
+  vortex.cu     vortex intensity and centres (-fmad=false)
 Host code is built with -ffp-contract=off so that the geometry builder's
 floating-point decisions do not depend on the host architecture.
 """
@@ -33,6 +34,7 @@ UNITS = [
     ("step_lp.cu", []),
     ("geometry.cpp", []),
     ("noalloc.cu", []),
+    ("vortex.cu", ["-fmad=false"]),
 ]
 
 

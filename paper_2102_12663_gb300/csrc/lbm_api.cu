@@ -1026,6 +1026,24 @@ bool domain_parts(const lbm_domain* d, const InstDesc** desc, int* precision, in
     return true;
 }
 
+bool domain_vortex_parts(const lbm_domain* d, const uint8_t** mask, int* nx, int* ny,
+                         int* periodic_x, int* periodic_y, double** scratch,
+                         int64_t* scratch_doubles, double* dx_m, double* dt_s,
+                         cudaStream_t* stream) {
+    if (!d) { fail(LBM_EINVAL, "null domain"); return false; }
+    *mask = d->h.mask;
+    *nx = d->nx;
+    *ny = d->ny;
+    *periodic_x = d->periodic_x;
+    *periodic_y = d->periodic_y;
+    *scratch = d->h.partials;
+    *scratch_doubles = d->L.max_tiles * NPART;
+    *dx_m = d->have_params ? d->params.dx_m : 0.0;
+    *dt_s = d->have_params ? d->params.dt_s : 0.0;
+    *stream = d->stream;
+    return true;
+}
+
 void fill_observables(const lbm_domain* d, const double* o, lbm_observables* out) {
     fill_obs(d, o, d->step, out);
 }

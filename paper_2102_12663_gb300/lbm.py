@@ -83,6 +83,16 @@ class Observables(ctypes.Structure):
     ]
 
 
+class VortexInfo(ctypes.Structure):
+    _fields_ = [("intensity", ctypes.c_double), ("intensity_abs", ctypes.c_double),
+                ("intensity_phys", ctypes.c_double), ("intensity_abs_phys", ctypes.c_double),
+                ("psi_max", ctypes.c_double), ("psi_min", ctypes.c_double),
+                ("max_x", ctypes.c_int32), ("max_y", ctypes.c_int32),
+                ("min_x", ctypes.c_int32), ("min_y", ctypes.c_int32),
+                ("max_mm", ctypes.c_double * 2), ("min_mm", ctypes.c_double * 2),
+                ("n_fluid", ctypes.c_int64)]
+
+
 # lbm_launch.stepping
 STEP_FLOW = 0          # one cooperative dataflow launch for many steps
 STEP_PER_LAUNCH = 1    # one launch per step (CUDA-graph replay)
@@ -127,6 +137,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "lbm_read_observables": (i32, [dom, P(Observables)]),
         "lbm_read_observables_noalloc": (i32, [dom, P(Observables)]),
         "lbm_read_field": (i32, [dom, vp, vp, vp]),
+        "lbm_vortex": (i32, [dom, vp, P(VortexInfo)]),
         "lbm_read_populations": (i32, [dom, vp, vp]),
         "lbm_write_populations": (i32, [dom, vp, vp]),
         "lbm_state_bytes": (sz, [dom]),
@@ -336,6 +347,22 @@ class Domain:
         check(self._L.lbm_read_field(self._h, ctypes.c_void_p(u.data_ptr()),
                                      ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(T.data_ptr())))
         return u, p, T
+
+    def vortex(self, u=None) -> dict:
+        """Vortex intensity and centres (Eq. 18, Tab. 3) of the device velocity
+        field u[2, ny, nx] (float64; default: the current state's, from
+        fields())."""
+        if u is None:
+            u = self.fields()[0]
+        torch = _torch()
+        assert u.dtype == torch.float64 and u.is_cuda and u.is_contiguous()
+        assert tuple(u.shape) == (2, self.ny, self.nx)
+        o = VortexInfo()
+        check(self._L.lbm_vortex(self._h, ctypes.c_void_p(u.data_ptr()), ctypes.byref(o)))
+        out = {k: getattr(o, k) for k, _ in VortexInfo._fields_}
+        out["max_mm"] = tuple(o.max_mm)
+        out["min_mm"] = tuple(o.min_mm)
+        return out
 
     def populations(self):
         """(f[9, ny, nx], g[4, ny, nx]) float64 device tensors, natural order."""

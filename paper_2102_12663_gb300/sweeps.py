@@ -16,13 +16,14 @@ from . import lbm
 
 def steady_sweep(geometry: dict, params: dict, variants: list, precision: str = "f64",
                  tol: float = 1e-10, check_every: int = 100, max_steps: int = 2_000_000,
-                 launch: dict | None = None, device=None) -> list:
+                 launch: dict | None = None, device=None, vortex: bool = False) -> list:
     """Steady observables for each variant.
 
     geometry, params: the base eye (lbm.Domain geometry dict, lbm_params dict).
     variants: list of dicts; key "geometry" overrides geometry entries, every
     other key overrides a parameter.  Returns, per variant, the observables of
-    its last check plus "steps" and "converged"."""
+    its last check plus "steps" and "converged", and with vortex=True the
+    vortex measures of its final state (Eq. 18, Tab. 3) under "vortex"."""
     import torch
     dev = torch.device(device if device is not None else "cuda")
     stream = torch.cuda.Stream(device=dev)
@@ -49,6 +50,8 @@ def steady_sweep(geometry: dict, params: dict, variants: list, precision: str = 
                     converged = 0.0 <= o["residual"] < tol
                     if converged or o["nan_flag"] or d.step_count >= max_steps:
                         out[k] = dict(o, steps=d.step_count, converged=converged)
+                        if vortex:
+                            out[k]["vortex"] = d.vortex()
                         batch.remove(d)
                         del active[k]
         finally:

@@ -39,12 +39,13 @@ def test_library_exports_every_declared_entry_point(L):
 def test_struct_layout_matches_header(tmp_path):
     structs = {"lbm_geometry_desc": lbm.GeometryDesc, "lbm_geometry_info": lbm.GeometryInfo,
                "lbm_params": lbm.Params, "lbm_observables": lbm.Observables,
-               "lbm_launch": lbm.Launch}
+               "lbm_launch": lbm.Launch, "lbm_vortex_info": lbm.VortexInfo}
     body = "".join(f'printf("{k} %zu\\n", sizeof({k}));' for k in structs)
     fields = [("lbm_params", "seed"), ("lbm_params", "p_sc_pa"), ("lbm_observables", "nan_flag"),
               ("lbm_geometry_desc", "chamber_angle_deg"), ("lbm_geometry_desc", "host_mask"),
               ("lbm_geometry_info", "arc_xc"), ("lbm_params", "h_tm"),
-              ("lbm_observables", "u_seep"), ("lbm_launch", "stepping"), ("lbm_launch", "sweep_lag")]
+              ("lbm_observables", "u_seep"), ("lbm_launch", "stepping"), ("lbm_launch", "sweep_lag"),
+              ("lbm_vortex_info", "max_mm"), ("lbm_vortex_info", "n_fluid")]
     body += "".join(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));' for s, f in fields)
     body += 'printf("STEP_FLOW %d\\n", LBM_STEP_FLOW);printf("STEP_PER_LAUNCH %d\\n", LBM_STEP_PER_LAUNCH);'
     c = tmp_path / "probe.c"

@@ -7,7 +7,9 @@ not its value:
   Tab. 6  IOP rises with the viscosity;
   Tab. 7  IOP rises as the chamber angle narrows;
   Tab. 8  wall shear grows with the temperature difference, and a standing eye
-          has higher cornea wall shear than an up-facing one."""
+          has higher cornea wall shear than an up-facing one;
+  Tab. 3  the vortex intensity (Eq. 18) grows with the temperature difference,
+          and an up-facing eye carries two mirror-image vortices."""
 import numpy as np
 import pytest
 
@@ -68,9 +70,17 @@ def test_wall_shear_grows_with_temperature_difference_and_orientation():
     dts = [0.5, 1.0, 2.0]
     variants = [dict(g_beta=gb, g_dir=W.UPRIGHT, T_hot=dt, T_in=dt, T0=0.5 * dt) for dt in dts]
     variants.append(dict(g_beta=gb, g_dir=W.SUPINE, T_hot=2.0, T_in=2.0, T0=1.0))
-    res = sweeps.steady_sweep(GEO, base(), variants, tol=1e-9)
+    res = sweeps.steady_sweep(GEO, base(), variants, tol=1e-9, vortex=True)
     assert all(r["converged"] for r in res)
     wc = np.array([r["wss_cornea"] for r in res[:3]])
     wi = np.array([r["wss_iris"] for r in res[:3]])
     assert np.all(np.diff(wc) > 0) and np.all(np.diff(wi) > 0)
     assert res[2]["wss_cornea"] > res[3]["wss_cornea"]  # standing above up-facing
+    # Tab. 3: intensity grows with the temperature difference
+    vi = np.array([r["vortex"]["intensity_abs"] for r in res[:3]])
+    assert np.all(np.diff(vi) > 0)
+    # up-facing (Sec. 3.4): two vortices, mirror images about the mid-plane
+    v = res[3]["vortex"]
+    assert v["max_x"] + v["min_x"] == GEO["nx"] - 1 and v["max_y"] == v["min_y"]
+    assert v["psi_max"] > 0 > v["psi_min"]
+    assert v["psi_max"] == pytest.approx(-v["psi_min"], rel=1e-6)
