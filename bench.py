@@ -341,8 +341,11 @@ def run_gpu(args):
     return 0
 
 
-LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0, sweep_steps=1,
+# the FP32 4096 x 2048 line: 64 x 8 tiles, one dataflow launch per check interval
+LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=1, sweep_steps=1,
               sweep_lag=0)
+# the studies (other grid sizes and many small grids): one launch per step
+STUDY_LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):
@@ -381,7 +384,7 @@ def run_precision(args):
         st = torch.cuda.Stream()
         dom = lbm.Domain(dict(nx=cfg["nx"], ny=cfg["ny"], angle_deg=cfg["angle_deg"]),
                          precision=prec, stream=st)
-        dom.set_launch(**LAUNCH)
+        dom.set_launch(**STUDY_LAUNCH)
         dom.set_params(W.config_params(cfg))
         with torch.cuda.stream(st):
             _time_intervals(dom, 3)
@@ -409,7 +412,7 @@ def run_precision(args):
         obs, total, u_steady, oracle_rel = {}, None, None, None
         for prec in ("f64", "f32", "f16", "bf16"):
             dom = lbm.Domain(dict(nx=nx, ny=ny, angle_deg=cfg["angle_deg"]), precision=prec)
-            dom.set_launch(**LAUNCH)
+            dom.set_launch(**STUDY_LAUNCH)
             dom.set_params(pp)
             if prec == "f64":
                 # tie the FP64 path to the oracle on this grid
@@ -473,7 +476,8 @@ def run_precision(args):
 
 def run_batch(args):
     """64 uneven eye instances (NY log-uniform 128..1024, seeded parameters)
-    in one batch: one launch per step, graph-replayed, autotuned shape;
+    in one batch (autotuned shape and stepping: one dataflow launch per check
+    interval or one launch per step, graph-replayed);
     against the same instances stepped one after the other."""
     import torch
 
@@ -486,10 +490,10 @@ def run_batch(args):
     doms = []
     for i in insts:
         d = lbm.Domain(dict(nx=i["nx"], ny=i["ny"], angle_deg=i["angle_deg"]), precision="f32", stream=st)
-        d.set_launch(**LAUNCH)
+        d.set_launch(**STUDY_LAUNCH)
         d.set_params(i["params"])
         doms.append(d)
-    b = lbm.Batch("f32", max_instances=64, max_tiles=1 << 21, launch=LAUNCH, stream=st)
+    b = lbm.Batch("f32", max_instances=64, max_tiles=1 << 21, launch=STUDY_LAUNCH, stream=st)
     for d in doms:
         b.add(d)
     with torch.cuda.stream(st):
@@ -544,14 +548,14 @@ def run_serve(args):
     draws = W.request_stream(args.requests, rate_hz=20.0, ny_lo=128, ny_hi=2048, fp16_share=0.5)
     reqs = serve.requests_from_draws(draws)
     srv = serve.Server(budget_bytes=150e9, tol=1e-7, check_every=CHECK, max_steps=args.cap,
-                       launch=LAUNCH)
+                       launch=STUDY_LAUNCH)
     res = srv.run(reqs, realtime=True)
     s_served = serve.summary(res, srv.wall_s)
     s_served["peak_hbm_bytes"] = srv.peak_used
     s_served["cell_updates_per_s"] = srv.cell_updates / srv.wall_s
     srv.close()
     base = serve.solve_one_at_a_time(serve.requests_from_draws(draws), tol=1e-7, check_every=CHECK,
-                                     max_steps=args.cap, launch=LAUNCH, realtime=True)
+                                     max_steps=args.cap, launch=STUDY_LAUNCH, realtime=True)
     wall = max(r.finish_s for r in base)
     s_base = serve.summary(base, wall)
     line = {"metric": "served steady solves per second", "value": s_served["solves_per_s"],

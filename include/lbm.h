@@ -176,7 +176,10 @@ typedef struct lbm_observables {
  * storages) and row group.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
  * <= 256, tile area >= 128 cells.
  *
- * stepping selects how lbm_step advances a domain:
+ * stepping selects how lbm_step advances a domain (the zero default is one
+ * launch per step; the dataflow launch is faster where the per-step launch
+ * overhead is a large share of a step, e.g. 0.81 against 0.74 of HBM on a
+ * 4096 x 2048 eye, and slower on much smaller or much larger grids):
  *   LBM_STEP_FLOW: one cooperative launch covers all the steps of the call.  No
  *     grid-wide barrier separates them: a tile starts step s as soon as it
  *     and its eight neighbour tiles have finished step s - 1 (each link
@@ -196,11 +199,11 @@ typedef struct lbm_observables {
  * The dataflow kernel (any sweep) and the per-step direct kernel give
  * bit-identical populations.  Observing steps and batches always take one
  * launch per step. */
-enum { LBM_STEP_FLOW = 0, LBM_STEP_PER_LAUNCH = 1 };
+enum { LBM_STEP_PER_LAUNCH = 0, LBM_STEP_FLOW = 1 };
 
 typedef struct lbm_launch {
     int32_t tile_w, block_rows, rows_per_thread, blocks_per_sm;
-    int32_t stepping;    /* LBM_STEP_FLOW or LBM_STEP_PER_LAUNCH */
+    int32_t stepping;    /* LBM_STEP_PER_LAUNCH (0) or LBM_STEP_FLOW */
     int32_t sweep_steps; /* LBM_STEP_FLOW: steps per wavefront sweep, 0..8 */
     int32_t sweep_lag;   /* LBM_STEP_FLOW: tile rows between a sweep's steps */
 } lbm_launch;
@@ -326,17 +329,19 @@ typedef struct lbm_vortex_info {
  * region). */
 lbm_status lbm_vortex(lbm_domain* dom, const double* dev_u, lbm_vortex_info* out);
 
-/* ---- batches: many problems, one launch per time step --------------------
+/* ---- batches: many problems, fused launches ---------------------------------
  * A batch advances many domains of one storage precision, of any sizes and
- * parameters, with a single launch of the fused step per time step over the
- * concatenated tile lists of its members (and, for 32 or more steps, replays
+ * parameters, over the concatenated tile lists of its members: with dataflow
+ * stepping one cooperative launch for all steps of a call, else a single
+ * launch of the fused step per time step (and, for 32 or more steps, replays
  * of a CUDA graph of those launches).  Each member keeps its own state,
  * parameters and step counter; a member's results do not depend on which
  * other domains share the batch: populations are bit-identical to stepping it
  * alone with the same launch shape, and its observables are folded from its
  * own tiles in a fixed order.  While a domain belongs to a batch its work
  * runs on the batch's stream.  Device memory of the batch (member table,
- * tile list, observables) belongs to the caller: lbm_batch_bytes. */
+ * tile list, neighbour lists, progress words, observables) belongs to the
+ * caller: lbm_batch_bytes. */
 
 /* Bytes for a batch of up to max_instances members holding max_tiles tiles
  * in total (sum of lbm_get_tile_count of the members at the batch's shape). */
@@ -357,7 +362,9 @@ lbm_status lbm_batch_remove(lbm_batch* b, lbm_domain* dom);
 int32_t lbm_batch_size(const lbm_batch* b);
 
 /* Advance every member nsteps time steps (Eqs. 6 and 11 with all boundary
- * rules), one launch per step, asynchronously on the batch's stream. */
+ * rules), asynchronously on the batch's stream: with the batch shape's
+ * stepping LBM_STEP_FLOW one dataflow launch over all members (step by step;
+ * sweep_steps is ignored), else one launch per step. */
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
 
 /* One check interval of the steady-state loop for every member:

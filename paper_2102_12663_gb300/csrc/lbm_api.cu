@@ -151,7 +151,7 @@ struct lbm_domain {
     int flow_grid = 0;                // co-resident blocks of the dataflow kernel
     int ntiles = 0;
     int64_t tiled_cells = 0;
-    lbm_launch launch{128, 1, 2, 0, LBM_STEP_FLOW, 1, 0};
+    lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     lbm_params params{};
     bool have_params = false;
     int64_t step = 0;
@@ -159,6 +159,7 @@ struct lbm_domain {
     double last_iop = 0.0;            // IOP of the last steady-state check
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
     std::vector<int4> htiles;         // host copy of the tile list
+    std::vector<int> hnbr;            // host copy of the neighbour lists
     lbm_batch* batch = nullptr;       // batch this domain belongs to, if any
     cudaStream_t own_stream = nullptr;
     lbm_observables last_obs{};       // observables of the last batch check
@@ -252,6 +253,7 @@ static lbm_status build_tiles(lbm_domain* d) {
         }
     d->sweep_k = K;
     d->per_sweep = (int)items.size();
+    d->hnbr = nbr;
     d->ntiles = (int)tiles.size();
     d->tiled_cells = cells;
     d->h.ntiles = d->ntiles;
@@ -1064,17 +1066,22 @@ struct lbm_batch {
     InstDesc* d_table = nullptr;
     double* d_obs = nullptr;
     int4* d_tiles = nullptr;
+    int* d_nbr = nullptr;              // dataflow: 8 neighbour tiles per tile (batch indices)
+    int* d_flags = nullptr;            // dataflow: status, abort and progress words
+    int4* d_items = nullptr;           // dataflow: one item per tile, step by step
+    bool coop = false;
+    int flow_grid = 0;
     std::vector<lbm_domain*> members;  // table order
     std::vector<InstDesc> htable;
     std::vector<double> hobs;
-    lbm_launch launch{128, 1, 2, 0, LBM_STEP_FLOW, 1, 0};
+    lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     int ntiles = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
 };
 
 struct BatchLayout {
-    size_t table, obs, tiles, total;
+    size_t table, obs, tiles, nbr, flags, items, total;
 };
 
 static BatchLayout batch_layout(int max_inst, int64_t max_tiles) {
@@ -1083,6 +1090,9 @@ static BatchLayout batch_layout(int max_inst, int64_t max_tiles) {
     L.table = off; off = align_up(off + (size_t)max_inst * sizeof(InstDesc));
     L.obs = off; off = align_up(off + (size_t)max_inst * NOBS * sizeof(double));
     L.tiles = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
+    L.nbr = off; off = align_up(off + (size_t)max_tiles * 8 * sizeof(int));
+    L.flags = off; off = align_up(off + (size_t)(max_tiles + 2) * sizeof(int));
+    L.items = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
     L.total = off;
     return L;
 }
@@ -1114,10 +1124,16 @@ extern "C" lbm_status lbm_batch_create(int32_t precision, int32_t max_instances,
     b->d_table = reinterpret_cast<InstDesc*>(b->base + L.table);
     b->d_obs = reinterpret_cast<double*>(b->base + L.obs);
     b->d_tiles = reinterpret_cast<int4*>(b->base + L.tiles);
+    b->d_nbr = reinterpret_cast<int*>(b->base + L.nbr);
+    b->d_flags = reinterpret_cast<int*>(b->base + L.flags);
+    b->d_items = reinterpret_cast<int4*>(b->base + L.items);
     if (launch) b->launch = *launch;
-    int dev = 0;
+    int dev = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(int), b->stream);
+    b->coop = coop != 0;
     if (e != cudaSuccess) {
         delete b;
         return fail(LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
@@ -1167,16 +1183,45 @@ extern "C" lbm_status lbm_batch_remove(lbm_batch* b, lbm_domain* d) {
 
 extern "C" int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->members.size() : -1; }
 
-// merged tile list: member k's local tile t becomes (k, t, x0, y0)
+// merged tile list: member k's local tile t becomes (k, t, x0, y0); for
+// dataflow steps, the members' neighbour lists shifted to batch indices and
+// one work item per tile (batch index | TILE_PURE)
 static lbm_status batch_rebuild(lbm_batch* b) {
     if (!b->dirty) return LBM_OK;
-    std::vector<int4> tiles;
-    for (size_t k = 0; k < b->members.size(); ++k)
-        for (const int4& t : b->members[k]->htiles) tiles.push_back(make_int4((int)k, t.y, t.z, t.w));
+    std::vector<int4> tiles, items;
+    std::vector<int> nbr;
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        const lbm_domain* m = b->members[k];
+        const int base = (int)tiles.size();
+        for (size_t j = 0; j < m->htiles.size(); ++j) {
+            const int4& t = m->htiles[j];
+            const int g = base + (int)j;
+            tiles.push_back(make_int4((int)k, t.y, t.z, t.w));
+            items.push_back(make_int4((int)k, g | (t.y & TILE_PURE), t.z, t.w));
+            for (int i = 0; i < 8; ++i) {
+                const int u = m->hnbr[j * 8 + i];
+                nbr.push_back(u < 0 ? -1 : base + u);
+            }
+        }
+    }
     if ((int64_t)tiles.size() > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded");
-    if (!tiles.empty())
+    if (!tiles.empty()) {
         CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            b->stream));
+        CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           b->stream));
+    }
+    b->flow_grid = 0;
+    if (b->coop) {
+        const StepPlan pl = flow_plan(b->prec, shape_of(b->launch), false);
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.func,
+                                                         (int)(pl.block.x * pl.block.y), pl.smem));
+        if (b->launch.blocks_per_sm > 0) per_sm = std::min(per_sm, b->launch.blocks_per_sm);
+        b->flow_grid = per_sm * b->num_sms;
+    }
     CK(cudaStreamSynchronize(b->stream));
     b->ntiles = (int)tiles.size();
     batch_drop_graph(b);
@@ -1246,7 +1291,19 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     lbm_status st;
     if ((st = batch_rebuild(b)) != LBM_OK || (st = batch_upload_table(b)) != LBM_OK) return st;
     int64_t k = 0;
-    if (nsteps >= BATCH_GRAPH_STEPS && b->ntiles > 0) {
+    if (b->launch.stepping == LBM_STEP_FLOW && b->flow_grid > 0 && b->ntiles > 0) {
+        // dataflow launches, step by step (each member's own parity is in its
+        // table entry)
+        const int64_t chunk = (int64_t)INT32_MAX / 8 - 1;
+        while (k < nsteps) {
+            const int n = (int)std::min<int64_t>(nsteps - k, chunk);
+            FlowArgs fa{b->d_items, b->d_nbr, b->d_flags, b->ntiles, b->ntiles, 1, n, 0};
+            CK(launch_flow(b->prec, b->d_table, fa, shape_of(b->launch), false, b->flow_grid,
+                           b->stream));
+            k += n;
+        }
+    }
+    if (nsteps - k >= BATCH_GRAPH_STEPS && b->ntiles > 0) {
         if ((st = batch_ensure_graph(b)) != LBM_OK) return st;
         for (; nsteps - k >= BATCH_GRAPH_STEPS; k += BATCH_GRAPH_STEPS)
             CK(cudaGraphLaunch(b->graph, b->stream));
@@ -1276,6 +1333,15 @@ extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));
     if ((st = check_step_status()) != LBM_OK) return st;
+    {
+        int fs = 0;
+        CK(cudaMemcpyAsync(&fs, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        if (fs != 0) {
+            CK(cudaMemsetAsync(b->d_flags, 0, sizeof(int), b->stream));
+            return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
+        }
+    }
     for (int k = 0; k < n; ++k) {
         lbm_domain* m = b->members[k];
         // the observing step ran at step - 1 (pre-collision state of that step)
@@ -1338,9 +1404,13 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
     if (!b) return fail(LBM_EINVAL, "null batch");
     if (steps_per_candidate < 2) return fail(LBM_EINVAL, "steps_per_candidate must be >= 2");
     if (b->members.empty()) return fail(LBM_EINVAL, "empty batch");
+    // one launch per step on most shapes, dataflow stepping on the ones that suit it
     static const lbm_launch cand[] = {
-        {128, 2, 2, 0}, {64, 2, 2, 0}, {128, 2, 1, 0}, {64, 2, 4, 0}, {128, 1, 4, 0},
-        {128, 1, 8, 0}, {256, 1, 8, 0}, {128, 1, 16, 0}, {128, 2, 2, 8}, {64, 4, 1, 0}};
+        {128, 2, 2, 0, LBM_STEP_PER_LAUNCH}, {64, 2, 2, 0, LBM_STEP_PER_LAUNCH},
+        {64, 4, 1, 0, LBM_STEP_PER_LAUNCH},  {64, 4, 2, 0, LBM_STEP_PER_LAUNCH},
+        {128, 1, 4, 0, LBM_STEP_PER_LAUNCH}, {128, 1, 8, 0, LBM_STEP_PER_LAUNCH},
+        {256, 1, 8, 0, LBM_STEP_PER_LAUNCH}, {64, 4, 2, 0, LBM_STEP_FLOW},
+        {64, 4, 3, 0, LBM_STEP_FLOW},        {128, 2, 2, 0, LBM_STEP_FLOW}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -94,8 +94,8 @@ class VortexInfo(ctypes.Structure):
 
 
 # lbm_launch.stepping
-STEP_FLOW = 0          # one cooperative dataflow launch for many steps
-STEP_PER_LAUNCH = 1    # one launch per step (CUDA-graph replay)
+STEP_PER_LAUNCH = 0    # one launch per step (CUDA-graph replay); the default
+STEP_FLOW = 1          # one cooperative dataflow launch for many steps
 
 
 class Launch(ctypes.Structure):
@@ -393,7 +393,7 @@ class Domain:
 
     # -- launch shape and introspection -----------------------------------
     def set_launch(self, tile_w=128, block_rows=2, rows_per_thread=1, blocks_per_sm=0,
-                   stepping=STEP_FLOW, sweep_steps=1, sweep_lag=0):
+                   stepping=STEP_PER_LAUNCH, sweep_steps=1, sweep_lag=0):
         check(self._L.lbm_set_launch(self._h, ctypes.byref(
             Launch(tile_w, block_rows, rows_per_thread, blocks_per_sm, stepping, sweep_steps,
                    sweep_lag))))

@@ -138,3 +138,25 @@ def test_batch_capacity_errors():
     assert e.value.status == lbm.EINVAL
     b.close()
     b2.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batch_dataflow_matches_per_launch_bitwise(prec):
+    """One dataflow launch over all members (each member's own parity, mixed
+    by a lone odd step before joining) against one launch per step, member
+    by member, bit for bit."""
+    inst = small_instances(4, seed=13)
+    out = []
+    for stepping in (lbm.STEP_FLOW, lbm.STEP_PER_LAUNCH):
+        shape = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=stepping)
+        doms = [make(i, prec) for i in inst]
+        doms[2].step(1)
+        b = lbm.Batch(prec, max_instances=4, max_tiles=1 << 16, launch=shape)
+        for d in doms:
+            b.add(d)
+        b.step(37)
+        b.check(20)
+        out.append([pops(d) for d in doms])
+        b.close()
+    for (fa, ga), (fb, gb) in zip(*out):
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
