@@ -43,6 +43,7 @@ class Geom(ctypes.Structure):
         ("inlet_lo", ctypes.c_int32), ("inlet_width", ctypes.c_int32),
         ("eye_normals", ctypes.c_int32), ("outlet_axis", ctypes.c_int32),
         ("arc_xc", ctypes.c_double), ("arc_yc", ctypes.c_double),
+        ("arc_r", ctypes.c_double),
     ]
 
 
@@ -55,7 +56,7 @@ class Params(ctypes.Structure):
         ("u_in_max", ctypes.c_double), ("K", ctypes.c_double),
         ("p_out", ctypes.c_double), ("drive", ctypes.c_double * 2),
         ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("tm_model", ctypes.c_int32), ("pad0", ctypes.c_int32), ("u_seep", ctypes.c_double),
+        ("tm_model", ctypes.c_int32), ("bouzidi", ctypes.c_int32), ("u_seep", ctypes.c_double),
     ]
 
 
@@ -115,6 +116,8 @@ def lib() -> ctypes.CDLL:
         L.orc_seepage_velocity.restype = ctypes.c_double
         L.orc_seepage_velocity.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double]
         L.orc_set_threads.argtypes = [ctypes.c_int32]
+        L.orc_link_q.argtypes = [ctypes.POINTER(Geom), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.orc_link_q.restype = ctypes.c_double
         L.orc_vortex.argtypes = [ctypes.POINTER(Geom), u8p, dp, ctypes.POINTER(VortexOut)]
         L.orc_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -160,6 +163,7 @@ def make_params(**kw) -> Params:
     P.noise_amp = kw.get("noise_amp", 0.0)
     P.seed = int(kw.get("seed", 0)) & (2**64 - 1)
     P.tm_model = int(kw.get("tm_model", 0))
+    P.bouzidi = int(kw.get("bouzidi", 0))
     P.u_seep = float(kw.get("u_seep", 0.0))
     return P
 
@@ -178,8 +182,12 @@ def eye_mask(nx: int, ny: int, angle_deg: float = 45.0, band: int = 0,
 
 def mask_geom(nx: int, ny: int, periodic_x: int = 0, periodic_y: int = 0,
               inlet_dir=(0, 1), inlet_profile: int = 0, inlet_lo: int = 0,
-              inlet_width: int = 1, outlet_axis: int | None = None) -> Geom:
+              inlet_width: int = 1, outlet_axis: int | None = None, arc=None) -> Geom:
+    """Geometry of a caller mask; arc = (xc, yc, r) makes the cold cells' wall
+    the circle of that centre and radius (interpolated bounce-back)."""
     g = Geom()
+    if arc is not None:
+        g.arc_xc, g.arc_yc, g.arc_r = (float(v) for v in arc)
     g.outlet_axis = (0 if inlet_dir[0] != 0 else 1) if outlet_axis is None else outlet_axis
     g.nx, g.ny = nx, ny
     g.periodic_x, g.periodic_y = periodic_x, periodic_y
@@ -188,6 +196,11 @@ def mask_geom(nx: int, ny: int, periodic_x: int = 0, periodic_y: int = 0,
     g.inlet_lo, g.inlet_width = inlet_lo, inlet_width
     g.eye_normals = 0
     return g
+
+
+def link_q(geom: Geom, x: int, y: int, i: int) -> float:
+    """Fraction of link i from cell (x, y) at which it meets the cold wall's circle."""
+    return float(lib().orc_link_q(ctypes.byref(geom), int(x), int(y), int(i)))
 
 
 def seepage_velocity(params: Params, iop: float, h_tm: float) -> float:

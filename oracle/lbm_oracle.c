@@ -16,7 +16,9 @@
  *     sum_i e_i F_i = F for gravity in any direction, plus an optional uniform
  *     drive used by the closed-form test flows;
  *   - Eq. 11 read as the standard BGK update;
- *   - no-slip walls: halfway bounce-back (Bouzidi's scheme at q = 1/2);
+ *   - no-slip walls: halfway bounce-back (Bouzidi's scheme at q = 1/2); on
+ *     request, Bouzidi's linear interpolated rule on the curved cold wall
+ *     (the cornea circle), with q from the exact link-circle intersection;
  *   - inlet: moving-wall bounce-back; outlet: pressure anti-bounce-back;
  *   - thermal Dirichlet walls: anti-bounce-back ("extrapolation" at q = 1/2);
  *   - TM: porous cells with an implicit mid-step Darcy drag.
@@ -142,6 +144,7 @@ int orc_eye_mask(int32_t nx, int32_t ny, double angle_deg, int32_t band,
     geom->outlet_axis = 0;
     geom->arc_xc = xc;
     geom->arc_yc = yc;
+    geom->arc_r = R;
     return 0;
 }
 
@@ -256,6 +259,31 @@ static void gather(const double* f, const double* T, int64_t N, int64_t c,
     for (int i = 0; i < 4; ++i) gc[i] = T[i * N + c];
 }
 
+/* Fraction q of the link from cell centre (x, y) along e_i at which it
+ * leaves the circle of centre (arc_xc, arc_yc) and radius arc_r: the positive
+ * root t of |P + t e_i - C|^2 = R^2 (P inside, so c < 0), written with the
+ * half coefficient: a = |e_i|^2, bh = (P - C) . e_i, c = |P - C|^2 - R^2,
+ * t = (-bh + sqrt(bh^2 - a c)) / a. */
+double orc_link_q(const orc_geom* G, int32_t x, int32_t y, int32_t i)
+{
+    const double dx = x - G->arc_xc, dy = y - G->arc_yc;
+    const double a = (double)(EX[i] * EX[i] + EY[i] * EY[i]);
+    const double bh = dx * EX[i] + dy * EY[i];
+    const double c = dx * dx + dy * dy - G->arc_r * G->arc_r;
+    return (-bh + sqrt(bh * bh - a * c)) / a;
+}
+
+/* Post-collision populations of the active cell c (its own collision, as in
+ * orc_step). */
+static void post_collision(const orc_params* P, const uint8_t* type, const double* f,
+                           const double* T, int64_t N, int64_t c, double fs[9])
+{
+    double fc[9], gc[4], gs[4];
+    for (int i = 0; i < 9; ++i) fc[i] = f[i * N + c];
+    for (int i = 0; i < 4; ++i) gc[i] = T[i * N + c];
+    orc_collide(P, type[c] == ORC_POROUS && P->tm_model == 0, fc, gc, fs, gs);
+}
+
 void orc_step(const orc_geom* G, const orc_params* P, const uint8_t* type,
               const double* f, const double* T, double* fn, double* Tn,
               double* q_in_out, double* q_out_out)
@@ -304,6 +332,24 @@ void orc_step(const orc_geom* G, const orc_params* P, const uint8_t* type,
                     double v = -fs[i] + 2.0 * (kappa * P->p_out + W[i] * (4.5 * eu * eu - 1.5 * usq));
                     fn[o * N + c] = v;
                     q_out += fs[i] - v;
+                } else if (tn == ORC_COLD && P->bouzidi && G->arc_r > 0.0 &&
+                           type[c] == ORC_FLUID) {
+                    /* Bouzidi's linear interpolated bounce-back on the curved
+                     * cornea, the wall at fraction q of the link:
+                     *   q < 1/2: f_o(x) = 2q f*_i(x) + (1 - 2q) f*_i(x - e_i),
+                     *   q > 1/2: f_o(x) = f*_i(x) / (2q) + (2q - 1)/(2q) f*_o(x);
+                     * halfway at q = 1/2 and where x - e_i is not active. */
+                    double q = orc_link_q(G, x, y, i);
+                    int64_t up = neighbour(G, x, y, o);
+                    if (q < 0.5 && up >= 0 && is_active(type[up])) {
+                        double fu[9];
+                        post_collision(P, type, f, T, N, up, fu);
+                        fn[o * N + c] = (2.0 * q) * fs[i] + (1.0 - 2.0 * q) * fu[i];
+                    } else if (q > 0.5) {
+                        fn[o * N + c] = (1.0 / (2.0 * q)) * fs[i] + ((2.0 * q - 1.0) / (2.0 * q)) * fs[o];
+                    } else {
+                        fn[o * N + c] = fs[i];
+                    }
                 } else {
                     fn[o * N + c] = fs[i]; /* halfway bounce-back */
                 }

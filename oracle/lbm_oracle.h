@@ -30,6 +30,7 @@ typedef struct {
     int32_t eye_normals;              /* 1: analytic eye wall normals */
     int32_t outlet_axis;              /* 0: outlets drain along x, 1: along y */
     double arc_xc, arc_yc;            /* centre of the cornea arc (eye only) */
+    double arc_r;                     /* its radius; 0: no curved wall */
 } orc_geom;
 
 typedef struct {
@@ -47,7 +48,8 @@ typedef struct {
     uint64_t seed;
     int32_t tm_model;      /* 0: porous TM cells with Darcy drag; 1: the lumped
                               TM of Sec. 2.3 (seepage-velocity outflow) */
-    int32_t pad0;
+    int32_t bouzidi;       /* 1: interpolated bounce-back on the curved cold
+                              wall (the circle of orc_geom), 0: halfway */
     double u_seep;         /* lumped TM: current seepage speed out of the outlets */
 } orc_params;
 
@@ -78,6 +80,7 @@ void orc_observe(const orc_geom* G, const orc_params* P, const uint8_t* type,
                  const double* f, const double* T, const double* u_snap,
                  orc_obs* obs);
 double orc_seepage_velocity(const orc_params* P, double iop, double h_tm);
+double orc_link_q(const orc_geom* G, int32_t x, int32_t y, int32_t i);
 
 /* Vortex measures of a velocity field (Eq. 18, Tab. 3).  u holds u_x in
  * u[0..N) and u_y in u[N..2N) (values at non-active cells are ignored). */

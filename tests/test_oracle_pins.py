@@ -4,8 +4,9 @@ Each test checks the oracle against something other than itself: algebraic
 identities of Guo's incompressible equilibrium (Sec. 2.3, Eqs. 7-9), the
 transport coefficients of Eqs. 10 and 14 measured from decaying waves,
 closed-form flows (plane Poiseuille, uniform Darcy flow, Brinkman channel,
-Darcy pressure drop, pure conduction), the Rayleigh-Benard onset, the exact
-per-step mass balance, mirror symmetry, and published test vectors.
+Darcy pressure drop, pure conduction, Poiseuille flow against a wall at a
+fractional link position), the Rayleigh-Benard onset, the exact per-step mass
+balance, mirror symmetry, and published test vectors.
 """
 import math
 import os
@@ -410,3 +411,47 @@ def test_vortex_poiseuille_wall_stencil_and_ties():
     assert (v["max_x"], v["max_y"]) == (0, H)
     assert v["psi_min"] == pytest.approx(0.5 * prof[1], rel=1e-14)
     assert (v["min_x"], v["min_y"]) == (0, 1)
+
+
+# ---- interpolated bounce-back on a curved wall (Bouzidi, [36] of the paper) ---
+
+def test_link_q_closed_forms():
+    """Link fractions to a circle: an axis link from (10, 0) to the circle of
+    radius 10.3 about the origin meets it at 0.3; a diagonal link from (7, 7)
+    to the circle of radius 10 at t = sqrt(50) - 7."""
+    g = O.mask_geom(32, 32, arc=(0.0, 0.0, 10.3))
+    assert O.link_q(g, 10, 0, 1) == pytest.approx(0.3, abs=1e-14)
+    assert O.link_q(g, 0, 10, 2) == pytest.approx(0.3, abs=1e-14)
+    g = O.mask_geom(32, 32, arc=(0.0, 0.0, 10.0))
+    assert O.link_q(g, 7, 7, 5) == pytest.approx(math.sqrt(50.0) - 7.0, abs=1e-14)
+    assert O.link_q(g, -7, -7, 7) == pytest.approx(math.sqrt(50.0) - 7.0, abs=1e-14)
+
+
+def _fractional_wall_profile(H, q0, bouzidi, tau=0.8, G=1e-6):
+    """Channel with the halfway bottom wall at y = 1/2 and a flat top wall at
+    y = H + q0 (a circle of radius 1e5: its sag over the two columns is
+    1e-6 cells), fluid rows 1..H."""
+    m, d = W.channel(2, H)
+    R = 1e5
+    g = O.mask_geom(d["nx"], d["ny"], 1, 0, arc=(0.5, H + q0 - R, R))
+    s = O.State(g, O.make_params(tau=tau, drive=(G, 0.0), bouzidi=bouzidi), m)
+    nu = (2 * tau - 1) / 6
+    s.run(int(8 * H * H / nu))
+    u = s.fields()[0][0].reshape(d["ny"], d["nx"])[1:-1, 0]
+    y = np.arange(1, H + 1)
+    ex = G / (2 * nu) * (y - 0.5) * (H + q0 - y)
+    return np.abs(u - ex).max() / ex.max()
+
+
+@pytest.mark.parametrize("q0", [0.25, 0.75])
+def test_bouzidi_places_the_wall_second_order(q0):
+    """Plane Poiseuille between a halfway wall and a wall at fraction q0 of
+    the last link (both branches of the rule): the interpolated bounce-back
+    converges at second order to u = G/(2 nu)(y - 1/2)(H + q0 - y), while
+    halfway bounce-back, which puts the wall at H + 1/2, keeps a first-order
+    error."""
+    errs = [_fractional_wall_profile(H, q0, 1) for H in (8, 16, 32)]
+    for a, b in zip(errs, errs[1:]):
+        assert 3.0 < a / b < 5.0
+    halfway = _fractional_wall_profile(32, q0, 0)
+    assert errs[-1] < halfway / 10
