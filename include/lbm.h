@@ -111,6 +111,7 @@ typedef struct lbm_geometry_info {
                                 inflow axis */
     int32_t reserved;
     double arc_xc, arc_yc;   /* centre of the cornea arc (EYE) */
+    double arc_r;            /* its radius (EYE; 0 for MASK) */
 } lbm_geometry_info;
 
 /* Physical parameters (lattice units).  May change between steps.
@@ -135,7 +136,18 @@ typedef struct lbm_geometry_info {
  *               u_s = K_tm (IOP - p_out) / (nu h_tm) (Darcy's law across a
  *               meshwork of thickness h_tm with a linear pressure profile),
  *               re-evaluated from the IOP after every steady-state check.
- *  h_tm         effective meshwork thickness in cells (tm_model 1; > 0). */
+ *  h_tm         effective meshwork thickness in cells (tm_model 1; > 0).
+ *  bouzidi      0: halfway bounce-back on every no-slip wall; 1: Bouzidi's
+ *               linear interpolated bounce-back (the no-slip scheme the paper
+ *               names, Sec. 2.3 ref. 36) on the links from fluid cells to the
+ *               curved cornea of the analytic eye, with the wall at the exact
+ *               fraction q of each link where it crosses the cornea circle:
+ *               q < 1/2: f_o(x) = 2q f*_i(x) + (1 - 2q) f*_i(x - e_i);
+ *               q > 1/2: f_o(x) = f*_i(x)/(2q) + (2q - 1)/(2q) f*_o(x)
+ *               (halfway where x - e_i is not active).  No effect on MASK
+ *               geometries.  The q < 1/2 rule is applied when the cell next
+ *               reads its populations, so switching it mid-run moves the
+ *               switch by one step on those links. */
 typedef struct lbm_params {
     double tau, tau_T;
     double g_beta;
@@ -149,7 +161,7 @@ typedef struct lbm_params {
     uint64_t seed;
     double dx_m, dt_s, rho0, p_sc_pa;
     int32_t tm_model;
-    int32_t reserved;
+    int32_t bouzidi;
     double h_tm;
 } lbm_params;
 

@@ -89,6 +89,7 @@ static bool eye_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info
         info->outlet_axis = 0;
         info->arc_xc = x_mid;
         info->arc_yc = y_ctr;
+        info->arc_r = R;
     }
     return true;
 }

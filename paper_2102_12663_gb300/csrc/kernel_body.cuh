@@ -136,6 +136,32 @@ __device__ __forceinline__ void neighbours(const InstDesc& d, int x, int y, int*
     nb[8] = yd + xr;
 }
 
+// Curved-cell entry of cell (x, y) (a short scan of its column), or null.
+__device__ __forceinline__ const CurvedCell* curved_entry(const InstDesc& d, int x, int y) {
+    for (int k = d.qcol[x]; k < d.qcol[x + 1]; ++k)
+        if (d.qtab[k].y == y) return d.qtab + k;
+    return nullptr;
+}
+
+// Bouzidi's rule for a wall at fraction q < 1/2 of link i, applied when the
+// cell reads its populations: the slot of f_o (o = opp(i)) holds the cell's
+// own post-collision f*_i of the previous step (written there as halfway
+// bounce-back), and f_i holds f*_i of the upstream cell x - e_i, streamed in;
+// f_o = 2q f*_i(x) + (1 - 2q) f*_i(x - e_i).  Links with q < 1/2 always have
+// an active upstream cell, so the opposite link is no wall link of this kind
+// and the corrections of one cell do not feed each other.
+template <class V>
+__device__ __forceinline__ void bouzidi_read(const CurvedCell* ce, V* f) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const double q = ce->q[i - 1];
+        if (q < 0.5) {
+            const V qq = V(q);
+            f[opp(i)] = (V(2.0) * qq) * f[opp(i)] + (V(1.0) - V(2.0) * qq) * f[i];
+        }
+    }
+}
+
 // Load the mask byte and the 13 populations of cell nb[0] (AA read pattern).
 // The mask and all populations are requested together (every slot index is
 // in range for any cell of the grid), so an active cell pays one memory round
@@ -189,6 +215,13 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     for (int i = 0; i < 9; ++i) f[i] = fin[i];
 #pragma unroll
     for (int i = 0; i < 4; ++i) g[i] = gin[i];
+    // interpolated bounce-back on the curved cornea (Bouzidi): q < 1/2 links
+    // are completed here, q > 1/2 links when they are written below
+    const CurvedCell* ce = nullptr;
+    if (d.bouzidi && (m & CURVED)) {
+        ce = curved_entry(d, x, y);
+        if (ce) bouzidi_read<E>(ce, f);
+    }
 
     // ---- moments, Eq. 9 and Eq. 13 ------------------------------------------
     const E ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
@@ -380,8 +413,17 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                 v = -fs[i] + E(2.0) * (kap * E(ph.p_out) +
                                        E(wgt(i)) * (E(4.5) * eu[i] * eu[i] - E(1.5) * usq));
                 if (OBS) q_out += (double)(fs[i] - v).v;
+            } else if (tn == COLD && ce) {
+                // curved cornea, wall beyond the link's midpoint (q > 1/2):
+                // f_o = f*_i / (2q) + (2q - 1)/(2q) f*_o; q < 1/2 stays halfway
+                // here and is completed when the cell next reads its populations
+                const double q = ce->q[i - 1];
+                if (q > 0.5) {
+                    const E qq = E(q);
+                    v = (E(1.0) / (E(2.0) * qq)) * fs[i] + ((E(2.0) * qq - E(1.0)) / (E(2.0) * qq)) * fs[opp(i)];
+                }
             }
-            // any wall: halfway bounce-back, v = f*_i
+            // any other wall: halfway bounce-back, v = f*_i
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;  // even+stream or odd+boundary

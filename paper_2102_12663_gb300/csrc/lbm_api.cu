@@ -92,7 +92,8 @@ static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct Layout {
     int64_t npad, max_tiles;
-    size_t desc, obs, mask, tiles, nbr, flags, items, partials, usnap, pops, total;
+    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, total;
+    int64_t max_curved;
 };
 
 static int64_t max_tiles_for(int nx, int ny) {
@@ -120,6 +121,10 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.nbr = off; off = align_up(off + (size_t)L.max_tiles * 8 * sizeof(int));
     L.flags = off; off = align_up(off + (size_t)(L.max_tiles + 2) * sizeof(int));
     L.items = off; off = align_up(off + (size_t)SWEEP_MAX * L.max_tiles * sizeof(int4));
+    // curved cornea cells: a few per column of the arc
+    L.max_curved = 4 * ((int64_t)nx + ny) + 64;
+    L.qcol = off; off = align_up(off + (size_t)(nx + 1) * sizeof(int32_t));
+    L.qtab = off; off = align_up(off + (size_t)L.max_curved * sizeof(CurvedCell));
     L.partials = off; off = align_up(off + (size_t)L.max_tiles * NPART * sizeof(double));
     L.usnap = off; off = align_up(off + 2 * (size_t)L.npad * real_size(prec));
     L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
@@ -160,6 +165,7 @@ struct lbm_domain {
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
     std::vector<int4> htiles;         // host copy of the tile list
     std::vector<int> hnbr;            // host copy of the neighbour lists
+    int64_t n_curved = 0;             // cells with a curved-cornea link
     lbm_batch* batch = nullptr;       // batch this domain belongs to, if any
     cudaStream_t own_stream = nullptr;
     lbm_observables last_obs{};       // observables of the last batch check
@@ -281,6 +287,72 @@ static lbm_status build_tiles(lbm_domain* d) {
     return LBM_OK;
 }
 
+// Link fractions of the fluid cells next to the curved cornea of the analytic
+// eye (Bouzidi's interpolated bounce-back): for each link i to a cold cell,
+// the fraction q at which it leaves the cornea circle, the positive root of
+// |P + t e_i - C|^2 = R^2 written with the half coefficient
+// (a = |e_i|^2, bh = (P - C).e_i, c = |P - C|^2 - R^2,
+// t = (-bh + sqrt(bh^2 - a c)) / a); q < 1/2 links whose upstream cell is not
+// active fall back to halfway (q = 1/2).  Cells with any q != 1/2 get the
+// CURVED mask bit and an entry, grouped by column.  Runs on the host before
+// the mask is uploaded.
+static lbm_status build_curved(lbm_domain* d) {
+    const int nx = d->nx, ny = d->ny;
+    std::vector<int32_t> qcol(nx + 1, 0);
+    std::vector<std::vector<CurvedCell>> cols(nx);
+    int64_t n = 0;
+    const double R = d->info.arc_r;
+    if (d->info.eye_normals && R > 0.0) {
+        static const int EXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        static const int EYh[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        auto type_at = [&](int x, int y) -> int {
+            if (x < 0 || x >= nx || y < 0 || y >= ny) return ADIABATIC;
+            return d->hmask[(int64_t)y * nx + x] & TYPE_BITS;
+        };
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                if (type_at(x, y) != FLUID) continue;
+                CurvedCell e{};
+                e.y = y;
+                bool any = false;
+                for (int i = 1; i < 9; ++i) {
+                    double q = 0.5;
+                    if (type_at(x + EXh[i], y + EYh[i]) == COLD) {
+                        const double dx = x - d->info.arc_xc, dy = y - d->info.arc_yc;
+                        const double a = (double)(EXh[i] * EXh[i] + EYh[i] * EYh[i]);
+                        const double bh = dx * EXh[i] + dy * EYh[i];
+                        const double c = dx * dx + dy * dy - R * R;
+                        q = (-bh + std::sqrt(bh * bh - a * c)) / a;
+                        if (q < 0.5 && type_at(x - EXh[i], y - EYh[i]) > POROUS) q = 0.5;
+                    }
+                    e.q[i - 1] = q;
+                    any = any || q != 0.5;
+                }
+                if (!any) continue;
+                cols[x].push_back(e);
+                d->hmask[(int64_t)y * nx + x] |= CURVED;
+                ++n;
+            }
+        }
+    }
+    if (n > d->L.max_curved) return fail(LBM_EINVAL, "curved-wall table overflow (%lld cells)", (long long)n);
+    std::vector<CurvedCell> tab;
+    tab.reserve((size_t)n);
+    for (int x = 0; x < nx; ++x) {
+        qcol[x] = (int32_t)tab.size();
+        tab.insert(tab.end(), cols[x].begin(), cols[x].end());
+    }
+    qcol[nx] = (int32_t)tab.size();
+    d->n_curved = n;
+    CK(cudaMemcpyAsync(d->base + d->L.qcol, qcol.data(), qcol.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, d->stream));
+    if (!tab.empty())
+        CK(cudaMemcpyAsync(d->base + d->L.qtab, tab.data(), tab.size() * sizeof(CurvedCell),
+                           cudaMemcpyHostToDevice, d->stream));
+    CK(cudaStreamSynchronize(d->stream));  // pageable sources
+    return LBM_OK;
+}
+
 static lbm_status upload_desc(lbm_domain* d) {
     CK(cudaMemcpyAsync(d->d_desc, &d->h, sizeof(InstDesc), cudaMemcpyHostToDevice, d->stream));
     return LBM_OK;
@@ -353,10 +425,19 @@ __global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, do
     const int64_t N = (int64_t)d.nx * d.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const bool act = (d.mask[c] & TYPE_BITS) <= POROUS;
+        const uint8_t m = d.mask[c];
+        const bool act = (m & TYPE_BITS) <= POROUS;
         const int x = (int)(c % d.nx), y = (int)(c / d.nx);
-        for (int i = 0; i < 9; ++i)
-            if (f) f[i * N + c] = act ? (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d) : 0.0;
+        if (f) {
+            double fv[9];
+            for (int i = 0; i < 9; ++i)
+                fv[i] = act ? (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d) : 0.0;
+            if (act && d.bouzidi && (m & CURVED)) {
+                const CurvedCell* ce = curved_entry(d, x, y);
+                if (ce) bouzidi_read<double>(ce, fv);
+            }
+            for (int i = 0; i < 9; ++i) f[i * N + c] = fv[i];
+        }
         for (int i = 1; i <= 4; ++i)
             if (g) g[(i - 1) * N + c] = act ? (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d) : 0.0;
     }
@@ -372,10 +453,23 @@ __global__ void write_pops_kernel(const InstDesc* __restrict__ dp, int parity, c
     const int64_t N = (int64_t)d.nx * d.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
-        if ((d.mask[c] & TYPE_BITS) > POROUS) continue;
+        const uint8_t m = d.mask[c];
+        if ((m & TYPE_BITS) > POROUS) continue;
         const int x = (int)(c % d.nx), y = (int)(c / d.nx);
-        if (f)
-            for (int i = 0; i < 9; ++i) ST::stf(P + slot_of(d, x, y, i, parity, false), (R)f[i * N + c], d);
+        if (f) {
+            double fv[9];
+            for (int i = 0; i < 9; ++i) fv[i] = f[i * N + c];
+            // curved cornea: store what the next read turns back into fv
+            // (the inverse of the q < 1/2 completion)
+            if (d.bouzidi && (m & CURVED)) {
+                const CurvedCell* ce = curved_entry(d, x, y);
+                for (int i = 1; ce && i < 9; ++i) {
+                    const double q = ce->q[i - 1];
+                    if (q < 0.5) fv[opp(i)] = (fv[opp(i)] - (1.0 - 2.0 * q) * fv[i]) / (2.0 * q);
+                }
+            }
+            for (int i = 0; i < 9; ++i) ST::stf(P + slot_of(d, x, y, i, parity, false), (R)fv[i], d);
+        }
         if (g)
             for (int i = 1; i <= 4; ++i) ST::stT(P + slot_of(d, x, y, i, parity, true), (R)g[(i - 1) * N + c], d);
     }
@@ -398,6 +492,10 @@ __global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, doubl
             double fv[9], gv[4];
             for (int i = 0; i < 9; ++i) fv[i] = (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d);
             for (int i = 1; i <= 4; ++i) gv[i - 1] = (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d);
+            if (d.bouzidi && (d.mask[c] & CURVED)) {
+                const CurvedCell* ce = curved_entry(d, x, y);
+                if (ce) bouzidi_read<double>(ce, fv);
+            }
             ux = fv[1] - fv[3] + fv[5] - fv[6] - fv[7] + fv[8];
             uy = fv[2] - fv[4] + fv[5] + fv[6] - fv[7] - fv[8];
             const double usq = ux * ux + uy * uy;
@@ -563,6 +661,12 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     h.fscale = precision == LBM_F16DEV ? 4096.0f : 1.0f;
     h.finv = 1.0f / h.fscale;
     lbm_status st;
+    if ((st = build_curved(d)) != LBM_OK) {
+        delete d;
+        return st;
+    }
+    h.qcol = reinterpret_cast<const int32_t*>(d->base + d->L.qcol);
+    h.qtab = reinterpret_cast<const CurvedCell*>(d->base + d->L.qtab);
     cudaError_t ce = cudaMemcpyAsync(d->base + d->L.mask, d->hmask.data(), (size_t)d->N,
                                      cudaMemcpyHostToDevice, d->stream);
     if (ce != cudaSuccess) {
@@ -625,7 +729,9 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     if (p->tm_model != 0 && p->tm_model != 1) return fail(LBM_EINVAL, "tm_model must be 0 or 1");
     if (p->tm_model == 1 && !(std::isfinite(p->h_tm) && p->h_tm > 0.0))
         return fail(LBM_EINVAL, "the lumped TM needs a positive thickness h_tm");
+    if (p->bouzidi != 0 && p->bouzidi != 1) return fail(LBM_EINVAL, "bouzidi must be 0 or 1");
     d->h.tm_model = p->tm_model;
+    d->h.bouzidi = p->bouzidi;
     Phys<double>& h = d->h.pd;
     h.omega = 1.0 / p->tau;
     h.omegaT = 1.0 / p->tau_T;

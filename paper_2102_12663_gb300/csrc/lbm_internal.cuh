@@ -14,6 +14,14 @@ namespace lbm {
 // of the eight neighbours is not an active (fluid or porous) cell.
 constexpr uint8_t TYPE_BITS = 7;
 constexpr uint8_t NEAR_BOUNDARY = 8;
+constexpr uint8_t CURVED = 16;  // fluid cell with a link to the curved cornea (q != 1/2)
+
+// Link fractions of one curved cell: q[i-1] for link i, 1/2 where the
+// halfway rule applies.  Entries are grouped by column (qcol prefix sums).
+struct CurvedCell {
+    int32_t y, pad;
+    double q[8];
+};
 enum : int { FLUID = 0, POROUS = 1, COLD = 2, HOT = 3, ADIABATIC = 4, INLET = 5, OUTLET = 6 };
 
 // Observation modes of the fused step (bit set).
@@ -71,7 +79,9 @@ struct InstDesc {
     int32_t eye_normals;
     int32_t tm_model;    // 0 porous TM cells, 1 lumped TM (seepage-velocity outlets)
     int32_t outlet_axis; // outlets drain along x (0) or y (1)
-    int32_t pad0;
+    int32_t bouzidi;     // interpolated bounce-back on the curved cornea
+    const int32_t* qcol; // nx + 1 prefix sums into qtab (curved cells per column)
+    const CurvedCell* qtab;
     double arc_xc, arc_yc;
     Phys<double> pd;
     Phys<float> pf;

@@ -50,7 +50,7 @@ class GeometryInfo(ctypes.Structure):
         ("inlet_profile", ctypes.c_int32), ("inlet_lo", ctypes.c_int32),
         ("inlet_width", ctypes.c_int32), ("eye_normals", ctypes.c_int32),
         ("outlet_axis", ctypes.c_int32), ("reserved", ctypes.c_int32),
-        ("arc_xc", ctypes.c_double), ("arc_yc", ctypes.c_double),
+        ("arc_xc", ctypes.c_double), ("arc_yc", ctypes.c_double), ("arc_r", ctypes.c_double),
     ]
 
 
@@ -65,7 +65,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("dx_m", ctypes.c_double), ("dt_s", ctypes.c_double), ("rho0", ctypes.c_double),
         ("p_sc_pa", ctypes.c_double),
-        ("tm_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("h_tm", ctypes.c_double),
+        ("tm_model", ctypes.c_int32), ("bouzidi", ctypes.c_int32), ("h_tm", ctypes.c_double),
     ]
 
 
@@ -247,6 +247,7 @@ def make_params(p: dict) -> Params:
     P.rho0 = p.get("rho0", 0.0)
     P.p_sc_pa = p.get("p_sc_pa", 0.0)
     P.tm_model = int(p.get("tm_model", 0))
+    P.bouzidi = int(p.get("bouzidi", 0))
     P.h_tm = float(p.get("h_tm", 0.0))
     return P
 

@@ -45,7 +45,8 @@ def test_struct_layout_matches_header(tmp_path):
               ("lbm_geometry_desc", "chamber_angle_deg"), ("lbm_geometry_desc", "host_mask"),
               ("lbm_geometry_info", "arc_xc"), ("lbm_params", "h_tm"),
               ("lbm_observables", "u_seep"), ("lbm_launch", "stepping"), ("lbm_launch", "sweep_lag"),
-              ("lbm_vortex_info", "max_mm"), ("lbm_vortex_info", "n_fluid")]
+              ("lbm_vortex_info", "max_mm"), ("lbm_vortex_info", "n_fluid"),
+              ("lbm_params", "bouzidi"), ("lbm_geometry_info", "arc_r")]
     body += "".join(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));' for s, f in fields)
     body += 'printf("STEP_FLOW %d\\n", LBM_STEP_FLOW);printf("STEP_PER_LAUNCH %d\\n", LBM_STEP_PER_LAUNCH);'
     c = tmp_path / "probe.c"
