@@ -116,6 +116,16 @@ __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPA
     }
 }
 
+// Programmatic dependent launch: allow the dependent grid to launch, and wait
+// until the prerequisite grid has completed with its memory visible.  Both
+// are no-ops for a kernel launched without a programmatic dependency.
+__device__ __forceinline__ void grid_dependents_go() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 // neighbour indices of cell (x, y) (wrap-around only ever triggers on
 // periodic edges: a non-periodic edge holds no active cell)
 __device__ __forceinline__ void neighbours(const InstDesc& d, int x, int y, int* nb) {
@@ -897,6 +907,10 @@ __global__ void __launch_bounds__(128) step_kernel_tma(const InstDesc* __restric
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    // programmatic dependent launch (graph replays): nothing is read before
+    // the previous step has completed
+    grid_dependents_go();
+    grid_dependency_wait();
     uint32_t seq = 0;  // rows this block has staged so far (same in every thread)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 te = tiles[t];
@@ -962,6 +976,9 @@ __global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kerne
     __shared__ double red[OBS ? 8 : 1][NPART];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
+    // programmatic dependent launch (graph replays): let the next step launch
+    // now; its blocks wait below until this grid has completed
+    grid_dependents_go();
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 te = tiles[t];
         __syncthreads();
@@ -971,6 +988,9 @@ __global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kerne
             for (int k = tid; k < (int)(sizeof(InstDesc) / 8); k += nthreads) dst[k] = src[k];
         }
         __syncthreads();
+        // the previous step (if launched as our programmatic prerequisite) has
+        // completed and its writes are visible before any population is touched
+        grid_dependency_wait();
         const int parity = (sd.parity ^ flip) & 1;
         double acc[NPART];
 #pragma unroll

@@ -822,33 +822,67 @@ static lbm_status step_once(lbm_domain* d, int mode) {
 
 // Builds (once per launch shape) a graph of GRAPH_STEPS chained plain steps
 // with alternating parity, replayed by lbm_step from an even step.
-static lbm_status ensure_graph(lbm_domain* d) {
-    if (d->graph) return LBM_OK;
-    cudaGraph_t g = nullptr;
-    CK(cudaGraphCreate(&g, 0));
-    const Shape sh = shape_of(d->launch);
-    const int grid = grid_of(d, d->ntiles);
-    cudaGraphNode_t prev = nullptr;
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k) {
-        const InstDesc* a0 = d->d_desc;
-        const int4* a1 = d->d_tiles;
-        int a2 = d->ntiles, a3 = k & 1, a4 = 0;
+// A CUDA graph of n chained plain steps with alternating parity.  The steps
+// are captured with programmatic dependent launch: step k + 1 may start while
+// step k drains, its blocks reading their tile entry and descriptor and then
+// waiting (griddepcontrol.wait) until step k has completed and its writes are
+// visible, so the launch latency and block ramp-up of each step overlap the
+// previous step's tail.  Falls back to plain dependencies where that is not
+// available.
+static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int4* tiles,
+                                      int ntiles, Shape sh, int grid, int nsteps, bool pdl,
+                                      cudaGraphExec_t* out) {
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return e;
+    }
+    const StepPlan pl = step_plan(prec, false, sh);
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        const InstDesc* a0 = insts;
+        const int4* a1 = tiles;
+        int a2 = ntiles, a3 = k & 1, a4 = 0;
         Shape a5 = sh;
         void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-        const StepPlan pl = step_plan(d->prec, false, sh);
-        cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void*>(pl.func);
-        kp.gridDim = dim3(grid);
-        kp.blockDim = pl.block;
-        kp.sharedMemBytes = (unsigned)pl.smem;
-        kp.kernelParams = args;
-        cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-        prev = node;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = pl.block;
+        cfg.dynamicSmemBytes = pl.smem;
+        cfg.stream = cs;
+        cfg.attrs = (pdl && k > 0) ? attr : nullptr;
+        cfg.numAttrs = (pdl && k > 0) ? 1 : 0;
+        e = cudaLaunchKernelExC(&cfg, pl.func, args);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&d->graph, g, 0);
-    cudaGraphDestroy(g);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+static cudaError_t step_graph(int prec, const InstDesc* insts, const int4* tiles, int ntiles,
+                              Shape sh, int grid, int nsteps, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaError_t e = capture_step_graph(prec, insts, tiles, ntiles, sh, grid, nsteps, true, out);
+    if (e == cudaSuccess) return e;
+    (void)cudaGetLastError();  // clear the failed attempt
+    *out = nullptr;
+    return capture_step_graph(prec, insts, tiles, ntiles, sh, grid, nsteps, false, out);
+}
+
+// GRAPH_STEPS plain steps from an even step, replayed by lbm_step
+static lbm_status ensure_graph(lbm_domain* d) {
+    if (d->graph) return LBM_OK;
+    const cudaError_t e = step_graph(d->prec, d->d_desc, d->d_tiles, d->ntiles, shape_of(d->launch),
+                                     grid_of(d, d->ntiles), GRAPH_STEPS, &d->graph);
     if (e != cudaSuccess) {
         d->graph = nullptr;
         return fail(LBM_ECUDA, "graph construction failed: %s", cudaGetErrorString(e));
@@ -1358,31 +1392,8 @@ static int batch_grid(const lbm_batch* b) {
 
 static lbm_status batch_ensure_graph(lbm_batch* b) {
     if (b->graph) return LBM_OK;
-    cudaGraph_t g = nullptr;
-    CK(cudaGraphCreate(&g, 0));
-    const Shape sh = shape_of(b->launch);
-    const int grid = batch_grid(b);
-    cudaGraphNode_t prev = nullptr;
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < BATCH_GRAPH_STEPS && e == cudaSuccess; ++k) {
-        const InstDesc* a0 = b->d_table;
-        const int4* a1 = b->d_tiles;
-        int a2 = b->ntiles, a3 = k & 1, a4 = 0;
-        Shape a5 = sh;
-        void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
-        const StepPlan pl = step_plan(b->prec, false, sh);
-        cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void*>(pl.func);
-        kp.gridDim = dim3(grid);
-        kp.blockDim = pl.block;
-        kp.sharedMemBytes = (unsigned)pl.smem;
-        kp.kernelParams = args;
-        cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-        prev = node;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
+    const cudaError_t e = step_graph(b->prec, b->d_table, b->d_tiles, b->ntiles, shape_of(b->launch),
+                                     batch_grid(b), BATCH_GRAPH_STEPS, &b->graph);
     if (e != cudaSuccess) {
         b->graph = nullptr;
         return fail(LBM_ECUDA, "batch graph construction failed: %s", cudaGetErrorString(e));
