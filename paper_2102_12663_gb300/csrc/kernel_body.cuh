@@ -542,6 +542,74 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const Ph
     f[12] = f[12] - omT * (f[12] - Tq * (1.0f - 2.0f * uy));
 }
 
+// Collision of a cell pair (cells x and x+1, 13 values each) and its AA-pattern
+// stores; every lane of the warp takes part (odd steps assemble x-shifted
+// links by shuffles).
+template <class ST, int PAR>
+__device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int y, float* a,
+                                                   float* b, bool por0, bool por1) {
+    using T = typename ST::T;
+    const int nx = d.nx, ny = d.ny;
+    const int np = (int)d.npad;
+    T* const P = static_cast<T*>(d.pops);
+    const int lane = threadIdx.x & 31;
+    const int row = y * nx;
+    const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
+    const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
+    const int xl = x == 0 ? nx - 1 : x - 1;
+    const int xr = x + 2 == nx ? 0 : x + 2;
+    collide_interior(a, por0, d.pf);
+    collide_interior(b, por1, d.pf);
+
+    // ---- store --------------------------------------------------------------
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+    } else {
+        ST::stf2(P + row + x, a[0], b[0], d);
+#pragma unroll
+        for (int k = 1; k < 13; ++k) {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;
+            const int pl = heat ? 8 + i : i;           // f*_i(x) goes to slot (x + e_i, i)
+            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
+            T* dst = P + pl * np + dr;
+            if (ex(i) == 0) {
+                if (heat) ST::stT2(dst + x, a[k], b[k], d);
+                else ST::stf2(dst + x, a[k], b[k], d);
+            } else if (ex(i) == 1) {  // destination columns x+1, x+2
+                const float left = __shfl_up_sync(0xffffffffu, b[k], 1);
+                if (lane != 0) {
+                    if (heat) ST::stT2(dst + x, left, a[k], d);
+                    else ST::stf2(dst + x, left, a[k], d);
+                } else {
+                    if (heat) ST::stT(dst + x + 1, a[k], d);
+                    else ST::stf(dst + x + 1, a[k], d);
+                }
+                if (lane == 31) {
+                    if (heat) ST::stT(dst + xr, b[k], d);
+                    else ST::stf(dst + xr, b[k], d);
+                }
+            } else {                  // destination columns x-1, x
+                const float right = __shfl_down_sync(0xffffffffu, a[k], 1);
+                if (lane != 31) {
+                    if (heat) ST::stT2(dst + x, b[k], right, d);
+                    else ST::stf2(dst + x, b[k], right, d);
+                } else {
+                    if (heat) ST::stT(dst + x, b[k], d);
+                    else ST::stf(dst + x, b[k], d);
+                }
+                if (lane == 0) {
+                    if (heat) ST::stT(dst + xl, a[k], d);
+                    else ST::stf(dst + xl, a[k], d);
+                }
+            }
+        }
+    }
+}
+
 template <class ST, int PAR>
 __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, int y, bool por0,
                                                      bool por1) {
@@ -602,56 +670,7 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
         }
     }
 
-    collide_interior(a, por0, d.pf);
-    collide_interior(b, por1, d.pf);
-
-    // ---- store --------------------------------------------------------------
-    if (PAR == 0) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
-#pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
-    } else {
-        ST::stf2(P + row + x, a[0], b[0], d);
-#pragma unroll
-        for (int k = 1; k < 13; ++k) {
-            const bool heat = k > 8;
-            const int i = heat ? k - 8 : k;
-            const int pl = heat ? 8 + i : i;           // f*_i(x) goes to slot (x + e_i, i)
-            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
-            T* dst = P + pl * np + dr;
-            if (ex(i) == 0) {
-                if (heat) ST::stT2(dst + x, a[k], b[k], d);
-                else ST::stf2(dst + x, a[k], b[k], d);
-            } else if (ex(i) == 1) {  // destination columns x+1, x+2
-                const float left = __shfl_up_sync(0xffffffffu, b[k], 1);
-                if (lane != 0) {
-                    if (heat) ST::stT2(dst + x, left, a[k], d);
-                    else ST::stf2(dst + x, left, a[k], d);
-                } else {
-                    if (heat) ST::stT(dst + x + 1, a[k], d);
-                    else ST::stf(dst + x + 1, a[k], d);
-                }
-                if (lane == 31) {
-                    if (heat) ST::stT(dst + xr, b[k], d);
-                    else ST::stf(dst + xr, b[k], d);
-                }
-            } else {                  // destination columns x-1, x
-                const float right = __shfl_down_sync(0xffffffffu, a[k], 1);
-                if (lane != 31) {
-                    if (heat) ST::stT2(dst + x, b[k], right, d);
-                    else ST::stf2(dst + x, b[k], right, d);
-                } else {
-                    if (heat) ST::stT(dst + x, b[k], d);
-                    else ST::stf(dst + x, b[k], d);
-                }
-                if (lane == 0) {
-                    if (heat) ST::stT(dst + xl, a[k], d);
-                    else ST::stf(dst + xl, a[k], d);
-                }
-            }
-        }
-    }
+    pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
 }
 
 template <class ST, bool OBS, int PAR>
