@@ -297,6 +297,14 @@ lbm_status lbm_load_state(lbm_domain* dom, const void* host_buf, size_t bytes);
 lbm_status lbm_set_launch(lbm_domain* dom, const lbm_launch* launch);
 lbm_status lbm_get_launch(const lbm_domain* dom, lbm_launch* launch);
 
+/* Test hook of the dataflow stepping's failure path (the paper has no
+ * counterpart): while tile >= 0, this domain's dataflow launches never report
+ * that tile's progress, so every wait on it runs out of its bounded polls
+ * (about a second), the launch aborts its other waits and completes, and the
+ * next observable read returns LBM_ECUDA ("results are invalid").  The GPU
+ * context stays usable.  -1 turns it off.  EINVAL for a tile out of range. */
+lbm_status lbm_debug_stall_tile(lbm_domain* dom, int32_t tile);
+
 /* Time step counter, geometry summary, number of tiles of the launch shape. */
 int64_t lbm_get_step(const lbm_domain* dom);
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_geometry_info* info);

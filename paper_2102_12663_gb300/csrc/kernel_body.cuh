@@ -29,8 +29,17 @@
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 3
 #endif
+// the same for the 16-bit storages (which convert on every load and store)
+#ifndef LBM_STEP_MIN_BLOCKS_16
+#define LBM_STEP_MIN_BLOCKS_16 3
+#endif
 
 namespace lbm {
+
+template <class ST>
+constexpr int step_min_blocks() {
+    return sizeof(typename ST::T) == 2 ? LBM_STEP_MIN_BLOCKS_16 : LBM_STEP_MIN_BLOCKS;
+}
 
 // Free constants of Eq. 7 (lambda + gamma = sigma, lambda + 2 gamma = 1/2)
 // and the D2Q9 weights of Eq. 8.
@@ -988,7 +997,7 @@ __global__ void __launch_bounds__(128) step_kernel_tma(const InstDesc* __restric
 }
 
 template <class ST, bool OBS>
-__global__ void __launch_bounds__(256, OBS ? 2 : LBM_STEP_MIN_BLOCKS) step_kernel(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(256, OBS ? 2 : step_min_blocks<ST>()) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
@@ -1080,7 +1089,7 @@ __device__ __forceinline__ void flow_wait(const int* done, int target, int* flag
 }
 
 template <class ST>
-__global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, step_min_blocks<ST>())
     step_kernel_flow(const InstDesc* __restrict__ insts, const FlowArgs fa, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -1115,7 +1124,7 @@ __global__ void __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
         __syncthreads();
         // a thread outside warp 0 reports, so that the release overlaps warp
         // 0's polls for the next item
-        if (tid == rel) st_release_gpu(done + t, s + 1);
+        if (tid == rel && t != fa.stall_tile) st_release_gpu(done + t, s + 1);
     }
 }
 

@@ -154,6 +154,7 @@ struct lbm_domain {
     bool periodic_x = false, periodic_y = false;
     bool coop = false;                // device supports cooperative launches
     int flow_grid = 0;                // co-resident blocks of the dataflow kernel
+    int stall_tile = -1;              // test hook (lbm_debug_stall_tile)
     int ntiles = 0;
     int64_t tiled_cells = 0;
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
@@ -902,7 +903,7 @@ extern "C" lbm_status lbm_step(lbm_domain* d, int64_t nsteps) {
         while (k < nsteps) {
             const int n = (int)std::min<int64_t>(nsteps - k, chunk);
             FlowArgs fa{d->d_items, d->d_nbr, d->d_flags, d->ntiles, d->per_sweep, d->sweep_k, n,
-                        (int)(d->step & 1)};
+                        (int)(d->step & 1), d->stall_tile};
             CK(launch_flow(d->prec, d->d_desc, fa, shape_of(d->launch), d->sweep_k > 1,
                            d->flow_grid, d->stream));
             d->step += n;
@@ -1136,6 +1137,13 @@ extern "C" lbm_status lbm_get_launch(const lbm_domain* d, lbm_launch* l) {
 }
 
 extern "C" int64_t lbm_get_step(const lbm_domain* d) { return d ? d->step : -1; }
+
+extern "C" lbm_status lbm_debug_stall_tile(lbm_domain* d, int32_t tile) {
+    if (!d) return fail(LBM_EINVAL, "null domain");
+    if (tile < -1 || tile >= d->ntiles) return fail(LBM_EINVAL, "tile %d out of range", tile);
+    d->stall_tile = tile;
+    return LBM_OK;
+}
 
 extern "C" lbm_status lbm_get_info(const lbm_domain* d, lbm_geometry_info* info) {
     if (!d || !info) return fail(LBM_EINVAL, "null argument");
@@ -1414,7 +1422,7 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
         const int64_t chunk = (int64_t)INT32_MAX / 8 - 1;
         while (k < nsteps) {
             const int n = (int)std::min<int64_t>(nsteps - k, chunk);
-            FlowArgs fa{b->d_items, b->d_nbr, b->d_flags, b->ntiles, b->ntiles, 1, n, 0};
+            FlowArgs fa{b->d_items, b->d_nbr, b->d_flags, b->ntiles, b->ntiles, 1, n, 0, -1};
             CK(launch_flow(b->prec, b->d_table, fa, shape_of(b->launch), false, b->flow_grid,
                            b->stream));
             k += n;

@@ -272,6 +272,7 @@ struct FlowArgs {
     const int* nbr;     // 8 neighbour tiles per tile, -1: none
     int* flags;         // status, abort, then one progress word per tile
     int ntiles, per_sweep, sweep_steps, nsteps, flip;
+    int stall_tile;     // test hook: this tile never reports progress (-1: none)
 };
 cudaError_t launch_flow(int precision, const InstDesc* insts, const FlowArgs& fa, Shape shape,
                         bool keep, int grid, cudaStream_t s);

@@ -146,6 +146,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "lbm_set_launch": (i32, [dom, P(Launch)]),
         "lbm_get_launch": (i32, [dom, P(Launch)]),
         "lbm_get_step": (i64, [dom]),
+        "lbm_debug_stall_tile": (i32, [dom, i32]),
         "lbm_get_info": (i32, [dom, P(GeometryInfo)]),
         "lbm_get_tile_count": (i64, [dom]),
         "lbm_step_bytes": (dbl, [dom]),
@@ -403,6 +404,10 @@ class Domain:
         l = Launch()
         check(self._L.lbm_get_launch(self._h, ctypes.byref(l)))
         return {k: getattr(l, k) for k, _ in Launch._fields_}
+
+    def debug_stall_tile(self, tile: int):
+        """Test hook: dataflow launches never report `tile` complete (-1: off)."""
+        check(self._L.lbm_debug_stall_tile(self._h, int(tile)))
 
     def info(self) -> dict:
         i = GeometryInfo()

@@ -171,3 +171,26 @@ def test_flow_fp64_matches_oracle():
     ref.run(333)
     f, t = pops(dom)
     assert np.array_equal(f.reshape(9, -1), ref.f) and np.array_equal(t.reshape(4, -1), ref.T)
+
+
+def test_expired_wait_is_reported_and_the_context_survives():
+    """The failure path of the bounded waits, made on the host: a tile that
+    never reports progress makes its neighbours' waits run out; the launch
+    aborts and completes, the next observable read reports the invalid
+    results, and the domain steps correctly again once the hook is off."""
+    launch = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0)
+    dom = eye_domain(192, 96, "f32", launch, lbm.STEP_FLOW)
+    dom.debug_stall_tile(dom.tile_count() // 2)
+    dom.step(3)
+    with pytest.raises(lbm.LBMError) as e:
+        dom.observables()
+    assert e.value.status == lbm.ECUDA and "too long" in str(e.value)
+    dom.debug_stall_tile(-1)
+    dom.reset()
+    ref = eye_domain(192, 96, "f32", launch, lbm.STEP_PER_LAUNCH)
+    dom.step(20)
+    ref.step(20)
+    fa, ga = pops(dom)
+    fb, gb = pops(ref)
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert dom.observables()["nan_flag"] == 0

@@ -267,13 +267,18 @@ def _patch_step_check(dom, x0, y0, w, h, info, pp):
     return np.abs(fn - fo).max() / scale, np.abs(gn - go).max() / np.abs(go).max()
 
 
-def test_full_size_fp32_sampled_windows():
-    """4096 x 2048 FP32 eye in the benchmark's launch shape: after 2,000
-    steps, windows at the inlet, the trabecular meshwork, the cornea apex and
-    the chamber interior match one oracle step computed from the same state."""
+@pytest.mark.parametrize("bench_launch", [True, False])
+def test_full_size_fp32_sampled_windows(bench_launch):
+    """4096 x 2048 FP32 eye in the benchmark's launch configuration (64 x 8
+    tiles, dataflow launches) and in the default one: after 2,000 steps,
+    windows at the inlet, the trabecular meshwork, the cornea apex and the
+    chamber interior match one oracle step computed from the same state."""
+    import bench
     nx, ny = 4096, 2048
     pp = W.config_params(W.CONFIG_FP32)
     dom = lbm.Domain(dict(nx=nx, ny=ny, angle_deg=45.0), precision="f32")
+    if bench_launch:
+        dom.set_launch(**bench.LAUNCH)
     dom.set_params(pp)
     dom.step(2000)
     info = dom.info()
