@@ -619,9 +619,60 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
     }
 }
 
-template <class ST, int PAR>
+// Observables of an interior cell pair before its collision (the observing
+// check step of the steady-state loop): mass, peak |u|^2, pressure sum and
+// count over fluid cells, NaN count, residual against and update of the
+// velocity snapshot.  Interior cells have no wall, inlet or outlet link, so
+// they add nothing to the wall shear stress or the fluxes.  Same definitions
+// as cell_body (Eq. 9), evaluated in the pair path's FP32 arithmetic.
+template <class ST>
+__device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, const float* a,
+                                             const float* b, uint32_t m2, int mode, double* acc) {
+    const int np = (int)d.npad;
+    const int c = y * d.nx + x;
+    float ux2[2], uy2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float* f = j == 0 ? a : b;
+        const float ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+        const float uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+        const float usq = ux * ux + uy * uy;
+        const float S0 = float(K_W0) * (-1.5f * usq);
+        const float sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+        const float p = (sum18 + S0) * 0.6f;
+        ux2[j] = ux;
+        uy2[j] = uy;
+        if (mode & OBS_STATS) {
+            acc[P_MASS] += (double)sum18;
+            acc[P_PEAK] = fmax(acc[P_PEAK], (double)usq);
+            if (((m2 >> (8 * j)) & TYPE_BITS) == FLUID) {
+                acc[P_SUM_P] += (double)p;
+                acc[P_N_FLUID] += 1.0;
+                if (!isfinite((double)p)) acc[P_NAN] += 1.0;
+            }
+        }
+    }
+    if (mode & (OBS_RESID | OBS_SNAP)) {
+        float* U = static_cast<float*>(d.usnap);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if ((mode & OBS_RESID) && d.snap_valid) {
+                const double dx = (double)ux2[j] - (double)U[c + j];
+                const double dy = (double)uy2[j] - (double)U[np + c + j];
+                acc[P_RESID] = fmax(acc[P_RESID], dx * dx + dy * dy);
+            }
+            if (mode & OBS_SNAP) {
+                U[c + j] = ux2[j];
+                U[np + c + j] = uy2[j];
+            }
+        }
+    }
+}
+
+template <class ST, int PAR, bool OBS = false>
 __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, int y, bool por0,
-                                                     bool por1) {
+                                                     bool por1, uint32_t m2 = 0, int mode = 0,
+                                                     double* acc = nullptr) {
     using T = typename ST::T;
     const int nx = d.nx, ny = d.ny;
     const int np = (int)d.npad;
@@ -679,6 +730,7 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
         }
     }
 
+    if constexpr (OBS) pair_observe<ST>(d, x, y, a, b, m2, mode, acc);
     pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
 }
 
@@ -688,8 +740,10 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
     constexpr int V = sizeof(typename ST::R) == 4 ? 2 : 1;
     const int x = te.z + V * threadIdx.x;
     if constexpr (V == 2) {
-        // the pair path needs whole warps on one row and even rows
-        const bool vec_ok = !OBS && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0;
+        // the pair path needs whole warps on one row and even rows; an
+        // observing step takes it too when it also writes (the steady-state
+        // check), while observe-only reads stay on the per-cell path
+        const bool vec_ok = (!OBS || (mode & OBS_WRITE)) && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0;
         // a pure tile (every cell fluid, in the grid, away from boundaries)
         // takes the pair path without reading its mask
         const bool pure = (te.y & TILE_PURE) != 0;
@@ -708,8 +762,9 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
                     fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
                 }
                 if (fast)
-                    update_pair_interior<ST, PAR>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
-                                                  (m2 & 0x100u) != 0 && sd.tm_model == 0);
+                    update_pair_interior<ST, PAR, OBS>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
+                                                       (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode,
+                                                       acc);
             }
             if (!fast) {
                 if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);

@@ -935,23 +935,23 @@ static lbm_status check_step_status() {
     return LBM_OK;
 }
 
-// Reads and clears the sticky status word of the domain's dataflow launches.
-static lbm_status check_flow_status(lbm_domain* d) {
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, d->d_flags, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
-    CK(cudaStreamSynchronize(d->stream));
-    if (st == 0) return LBM_OK;
-    CK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream));
-    return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
-}
-
+// Folds the observing step's partials and reads them back together with the
+// dataflow status word: one host synchronisation per observation.  The staged
+// kernels' status word is read only when this domain's shape may run them
+// (one launch per step, one row of threads per block, FP32 arithmetic).
 static lbm_status fetch_obs(lbm_domain* d, double* o) {
     CK(launch_finalize(d->d_desc, 1, d->stream));
     CK(cudaMemcpyAsync(o, d->d_obs, NOBS * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    int fst = 0;
+    CK(cudaMemcpyAsync(&fst, d->d_flags, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
     CK(cudaStreamSynchronize(d->stream));
-    lbm_status st = check_step_status();
-    if (st != LBM_OK) return st;
-    return check_flow_status(d);
+    if (d->prec != LBM_F64 && d->launch.block_rows == 1 && d->launch.stepping == LBM_STEP_PER_LAUNCH) {
+        const lbm_status st = check_step_status();
+        if (st != LBM_OK) return st;
+    }
+    if (fst == 0) return LBM_OK;
+    CK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream));
+    return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
 }
 
 static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out) {

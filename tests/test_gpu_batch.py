@@ -160,3 +160,29 @@ def test_batch_dataflow_matches_per_launch_bitwise(prec):
         b.close()
     for (fa, ga), (fb, gb) in zip(*out):
         assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_fp32_check_step_observables_match_the_oracle():
+    """The check step of an FP32 batch computes the observables of interior
+    cell pairs on the fast pair path and of boundary cells on the per-cell
+    path; both against the FP64 oracle within the FP32 tolerance."""
+    inst = small_instances(2, seed=17)
+    doms = [make(i, "f32") for i in inst]
+    b = lbm.Batch("f32", max_instances=2, max_tiles=1 << 16,
+                  launch=dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0))
+    for d in doms:
+        b.add(d)
+    b.step(45)
+    b.check(20)
+    for d, i in zip(doms, inst):
+        m, g = O.eye_mask(i["nx"], i["ny"], i["angle_deg"])
+        r = O.State(g, O.make_params(**i["params"]), m)
+        r.run(64)
+        oo = r.observe()
+        o = d.last_observables()
+        assert o["step"] == 64
+        for k, kr in [("iop", "iop"), ("mass", "mass"), ("peak_speed", "peak"),
+                      ("wss_cornea", "wss_cornea"), ("wss_iris", "wss_iris")]:
+            assert o[k] == pytest.approx(oo[kr], rel=2e-5), k
+        assert (o["n_fluid"], o["n_cornea"], o["n_iris"]) == (oo["n_fluid"], oo["n_cornea"], oo["n_iris"])
+    b.close()
