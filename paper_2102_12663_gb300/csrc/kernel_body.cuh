@@ -97,16 +97,27 @@ __device__ __forceinline__ Rn<R> operator-(Rn<R> a) { return Rn<R>(-a.v); }
 
 template <class R>
 __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPART], double* out) {
+    const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+    const int nwarps = (nthreads + 31) >> 5;
+    // lanes present in this warp (a block of fewer than 32 threads, or a last
+    // partial warp, has fewer)
+    const int width = min(32, nthreads - (warp << 5));
+    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
 #pragma unroll
     for (int k = 0; k < NPART; ++k) {
         double v = acc[k];
+        // most slots (wall shear, fluxes, counts of boundary cells) are zero
+        // in a whole warp away from the walls: skip their FP64 shuffle tree
+        if (__any_sync(mask, v != 0.0)) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double o = __shfl_down_sync(0xffffffffu, v, off);
-            v = k < NSUM ? v + o : fmax(v, o);
+            for (int off = 16; off > 0; off >>= 1) {
+                const double o = __shfl_down_sync(mask, v, off);
+                if (lane + off < width) v = k < NSUM ? v + o : fmax(v, o);
+            }
+        } else {
+            v = 0.0;
         }
         if (lane == 0) red[warp][k] = v;
     }
@@ -117,8 +128,8 @@ __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPA
             double v = lane < nwarps ? red[lane][k] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                double o = __shfl_down_sync(0xffffffffu, v, off);
-                v = k < NSUM ? v + o : fmax(v, o);
+                const double o = __shfl_down_sync(mask, v, off);
+                if (lane + off < width) v = k < NSUM ? v + o : fmax(v, o);
             }
             if (lane == 0) out[k] = v;
         }
@@ -624,13 +635,18 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
 // count over fluid cells, NaN count, residual against and update of the
 // velocity snapshot.  Interior cells have no wall, inlet or outlet link, so
 // they add nothing to the wall shear stress or the fluxes.  Same definitions
-// as cell_body (Eq. 9), evaluated in the pair path's FP32 arithmetic.
+// as cell_body (Eq. 9), evaluated in the pair path's FP32 arithmetic.  The
+// two cells are combined in FP32 first (a sum of two values, a maximum, a
+// count) and enter the FP64 partials once per pair: GB300's FP64 pipe is
+// narrow, and per-cell FP64 updates made this step FP64-bound.
 template <class ST>
 __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, const float* a,
                                              const float* b, uint32_t m2, int mode, double* acc) {
     const int np = (int)d.npad;
     const int c = y * d.nx + x;
-    float ux2[2], uy2[2];
+    float ux2[2], uy2[2], mass = 0.0f, psum = 0.0f, pk = 0.0f;
+    int nfl = 0;
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         const float* f = j == 0 ? a : b;
@@ -642,26 +658,36 @@ __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, co
         const float p = (sum18 + S0) * 0.6f;
         ux2[j] = ux;
         uy2[j] = uy;
-        if (mode & OBS_STATS) {
-            acc[P_MASS] += (double)sum18;
-            acc[P_PEAK] = fmax(acc[P_PEAK], (double)usq);
-            if (((m2 >> (8 * j)) & TYPE_BITS) == FLUID) {
-                acc[P_SUM_P] += (double)p;
-                acc[P_N_FLUID] += 1.0;
-                if (!isfinite((double)p)) acc[P_NAN] += 1.0;
-            }
+        mass += sum18;
+        pk = fmaxf(pk, usq);
+        if (((m2 >> (8 * j)) & TYPE_BITS) == FLUID) {
+            psum += p;
+            ++nfl;
+            bad = bad || !isfinite(p);
         }
+    }
+    if (mode & OBS_STATS) {
+        acc[P_MASS] += (double)mass;
+        acc[P_PEAK] = fmax(acc[P_PEAK], (double)pk);
+        acc[P_SUM_P] += (double)psum;
+        acc[P_N_FLUID] += (double)nfl;
+        if (bad) acc[P_NAN] += 1.0;
     }
     if (mode & (OBS_RESID | OBS_SNAP)) {
         float* U = static_cast<float*>(d.usnap);
+        if ((mode & OBS_RESID) && d.snap_valid) {
+            float r2 = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if ((mode & OBS_RESID) && d.snap_valid) {
-                const double dx = (double)ux2[j] - (double)U[c + j];
-                const double dy = (double)uy2[j] - (double)U[np + c + j];
-                acc[P_RESID] = fmax(acc[P_RESID], dx * dx + dy * dy);
+            for (int j = 0; j < 2; ++j) {
+                const float dx = ux2[j] - U[c + j];
+                const float dy = uy2[j] - U[np + c + j];
+                r2 = fmaxf(r2, dx * dx + dy * dy);
             }
-            if (mode & OBS_SNAP) {
+            acc[P_RESID] = fmax(acc[P_RESID], (double)r2);
+        }
+        if (mode & OBS_SNAP) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
                 U[c + j] = ux2[j];
                 U[np + c + j] = uy2[j];
             }

@@ -357,3 +357,22 @@ def test_supine_eye_mirror_symmetry_fp32():
     assert np.abs(ux + ux[:, ::-1]).max() <= 1e-5 * np.abs(ux).max()
     assert np.abs(uy - uy[:, ::-1]).max() <= 1e-5 * np.abs(uy).max()
     assert np.abs(T - T[:, ::-1]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("launch", [
+    dict(tile_w=32, block_rows=1, rows_per_thread=4, blocks_per_sm=0),   # 16-thread blocks
+    dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0),
+])
+def test_fp32_observables_any_block_width(launch):
+    """Observables of the FP32 eye through the check step (which also
+    writes) and through an observe-only read, for blocks narrower than a
+    warp and for full warps, against the oracle."""
+    dom, ref, _ = eye_pair(160, 80, "f32", launch=launch)
+    st, steps = dom.run_to_steady(0.0, check_every=60, max_steps=120)
+    assert steps == 120
+    ref.run(120)
+    o, oo = dom.observables(), ref.observe()
+    for k, kr in [("iop", "iop"), ("mass", "mass"), ("peak_speed", "peak"),
+                  ("wss_cornea", "wss_cornea"), ("wss_iris", "wss_iris")]:
+        assert o[k] == pytest.approx(oo[kr], rel=2e-5), k
+    assert o["residual"] > 0.0
