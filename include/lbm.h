@@ -264,8 +264,13 @@ lbm_status lbm_step(lbm_domain* dom, int64_t nsteps);
 /* Step until the largest change of |u| over check_every steps falls below tol
  * (the steady criterion max |du| < tol per check_every steps), or max_steps
  * have been taken.  *steps_out (may be NULL) receives the steps taken.
- * Returns ENOTCONVERGED at the cap and EUNSTABLE on a NaN.  Synchronises the
- * stream once per check. */
+ * Returns ENOTCONVERGED at the cap and EUNSTABLE on a NaN.  The host reads
+ * each check's observables from pinned memory while the next interval
+ * already runs (except with the lumped meshwork, tm_model 1, whose seepage
+ * speed needs each check before the next interval), so the loop may stop one
+ * interval after the check that met the criterion; *steps_out includes it.
+ * Returns with the stream synchronised.  Allocates a small pinned host
+ * buffer on first use. */
 lbm_status lbm_run_to_steady(lbm_domain* dom, double tol, int32_t check_every,
                              int64_t max_steps, int64_t* steps_out);
 

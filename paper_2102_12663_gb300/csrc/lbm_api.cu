@@ -155,6 +155,11 @@ struct lbm_domain {
     bool coop = false;                // device supports cooperative launches
     int flow_grid = 0;                // co-resident blocks of the dataflow kernel
     int stall_tile = -1;              // test hook (lbm_debug_stall_tile)
+    // steady-state loop: two pinned read-back slots of (observables, status)
+    // and their completion events, so that one interval can run while the
+    // host checks the previous one
+    double* pin = nullptr;
+    cudaEvent_t pin_ev[2] = {nullptr, nullptr};
     int ntiles = 0;
     int64_t tiled_cells = 0;
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
@@ -699,6 +704,9 @@ extern "C" void lbm_destroy_domain(lbm_domain* d) {
     if (d->batch) lbm_batch_remove(d->batch, d);
     cudaStreamSynchronize(d->stream);
     drop_graph(d);
+    if (d->pin) cudaFreeHost(d->pin);
+    for (cudaEvent_t e : d->pin_ev)
+        if (e) cudaEventDestroy(e);
     delete d;
 }
 
@@ -1002,32 +1010,111 @@ extern "C" lbm_status lbm_read_observables(lbm_domain* d, lbm_observables* out) 
     return LBM_OK;
 }
 
+// One check interval of the steady-state loop, enqueued: check_every - 1 plain
+// steps, the observing step, the fold of its partials and the read-back of
+// the observables and the dataflow status word into pinned slot `slot`.
+static constexpr int PIN_SLOT = NOBS + 1;  // doubles per slot (last: status word)
+
+static lbm_status enqueue_interval(lbm_domain* d, int32_t check_every, int slot) {
+    lbm_status st;
+    if ((st = lbm_step(d, check_every - 1)) != LBM_OK) return st;
+    const bool had_snap = d->h.snap_valid != 0;
+    if ((st = step_once(d, OBS_STATS | OBS_SNAP | OBS_WRITE | (had_snap ? OBS_RESID : 0))) != LBM_OK)
+        return st;
+    CK(launch_finalize(d->d_desc, 1, d->stream));
+    double* o = d->pin + slot * PIN_SLOT;
+    CK(cudaMemcpyAsync(o, d->d_obs, NOBS * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaMemcpyAsync(reinterpret_cast<int*>(o + NOBS), d->d_flags, sizeof(int),
+                       cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaEventRecord(d->pin_ev[slot], d->stream));
+    if (!had_snap) {  // a snapshot exists from this observing step on
+        d->h.snap_valid = 1;
+        if ((st = upload_desc(d)) != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check_every,
                                         int64_t max_steps, int64_t* steps_out) {
     if (!d) return fail(LBM_EINVAL, "null domain");
     if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
     if (check_every < 1 || max_steps < 0 || !(tol >= 0.0)) return fail(LBM_EINVAL, "bad steady-state arguments");
-    int64_t taken = 0;
-    lbm_status st = LBM_OK;
-    double o[NOBS];
-    if (steps_out) *steps_out = 0;
-    while (taken < max_steps) {
-        if ((st = lbm_step(d, check_every - 1)) != LBM_OK) return st;
-        const bool had_snap = d->h.snap_valid != 0;
-        if ((st = step_once(d, OBS_STATS | OBS_SNAP | OBS_WRITE | (had_snap ? OBS_RESID : 0))) != LBM_OK)
-            return st;
-        if ((st = fetch_obs(d, o)) != LBM_OK) return st;
-        taken += check_every;
-        if (steps_out) *steps_out = taken;
-        if (o[O_NAN] != 0.0) return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
-        update_seepage(d, o[O_IOP]);
-        if (d->h.tm_model == 1 || !had_snap) {
-            d->h.snap_valid = 1;
-            if ((st = upload_desc(d)) != LBM_OK) return st;
-        }
-        if (had_snap && o[O_RESID] < tol) return LBM_OK;
+    if (!d->pin) {
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&d->pin), 2 * PIN_SLOT * sizeof(double),
+                         cudaHostAllocDefault));
+        for (cudaEvent_t& e : d->pin_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    return fail(LBM_ENOTCONVERGED, "not steady after %lld steps", (long long)taken);
+    // The lumped meshwork feeds each check's IOP into the next interval, so it
+    // runs one interval at a time; otherwise the next interval is queued
+    // before the host reads a check, and the loop may stop one interval after
+    // the check that met the criterion (*steps_out counts it).
+    const bool ahead = d->h.tm_model != 1;
+    int64_t taken = 0, queued = 0;
+    int slot = 0;
+    lbm_status st = LBM_OK;
+    if (steps_out) *steps_out = 0;
+    auto drain = [&]() { cudaStreamSynchronize(d->stream); };
+    if (max_steps > 0) {
+        const bool had = d->h.snap_valid != 0;
+        if ((st = enqueue_interval(d, check_every, slot)) != LBM_OK) return st;
+        queued += check_every;
+        bool had_snap[2] = {had, true};
+        while (taken < max_steps) {
+            const int next = slot ^ 1;
+            const bool more = queued < max_steps;
+            if (ahead && more) {
+                had_snap[next] = d->h.snap_valid != 0;
+                if ((st = enqueue_interval(d, check_every, next)) != LBM_OK) { drain(); return st; }
+                queued += check_every;
+            }
+            CK(cudaEventSynchronize(d->pin_ev[slot]));
+            const double* o = d->pin + slot * PIN_SLOT;
+            const int fst = *reinterpret_cast<const int*>(o + NOBS);
+            taken += check_every;
+            if (steps_out) *steps_out = queued;
+            if (d->prec != LBM_F64 && d->launch.block_rows == 1 &&
+                d->launch.stepping == LBM_STEP_PER_LAUNCH && (st = check_step_status()) != LBM_OK) {
+                drain();
+                return st;
+            }
+            if (fst != 0) {
+                drain();
+                CK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream));
+                return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
+            }
+            if (o[O_NAN] != 0.0) {
+                drain();
+                return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
+            }
+            update_seepage(d, o[O_IOP]);
+            if (d->h.tm_model == 1) {
+                if ((st = upload_desc(d)) != LBM_OK) return st;
+            }
+            if (had_snap[slot] && o[O_RESID] < tol) {
+                drain();
+                if (queued > taken) {  // the interval queued ahead has run too: take its check
+                    const double* t = d->pin + next * PIN_SLOT;
+                    if (*reinterpret_cast<const int*>(t + NOBS) != 0) {
+                        CK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream));
+                        return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
+                    }
+                    if (t[O_NAN] != 0.0)
+                        return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)queued);
+                    update_seepage(d, t[O_IOP]);
+                }
+                return LBM_OK;
+            }
+            if (!ahead && more) {
+                had_snap[next] = d->h.snap_valid != 0;
+                if ((st = enqueue_interval(d, check_every, next)) != LBM_OK) return st;
+                queued += check_every;
+            }
+            slot = next;
+            if (taken >= queued) break;
+        }
+    }
+    drain();
+    return fail(LBM_ENOTCONVERGED, "not steady after %lld steps", (long long)queued);
 }
 
 // ---------------------------------------------------------------------------
