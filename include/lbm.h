@@ -206,8 +206,10 @@ typedef struct lbm_observables {
  *   LBM_STEP_PER_LAUNCH: one launch per step, replayed from a CUDA graph of
  *     32 steps; blocks_per_sm > 0 selects a grid of that many blocks per SM,
  *     0 one block per tile.  With FP32 arithmetic, shapes with block_rows 1
- *     take a kernel that stages population rows in shared memory by bulk
- *     copies; its interior collision rounds differently in the last bit.
+ *     and tile_w >= 64 take a persistent kernel (grid capped at the blocks
+ *     the device holds at once) whose warps stage population rows in shared
+ *     memory by bulk tensor copies; its interior collision rounds differently
+ *     in the last bit.
  * The dataflow kernel (any sweep) and the per-step direct kernel give
  * bit-identical populations.  Observing steps and batches always take one
  * launch per step. */

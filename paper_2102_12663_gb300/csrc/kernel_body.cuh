@@ -206,15 +206,15 @@ __device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, type
     m = d.mask[c];
     if (PAR == 0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = ST::ldf(P + i * np + c, d);
+        for (int i = 0; i < 9; ++i) f[i] = ST::ldf(P + plane_slot(i) * np + c, d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + (8 + i) * np + c, d);
+        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + plane_slot(8 + i) * np + c, d);
     } else {
-        f[0] = ST::ldf(P + c, d);
+        f[0] = ST::ldf(P + plane_slot(0) * np + c, d);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = ST::ldf(P + opp(i) * np + nb[opp(i)], d);
+        for (int i = 1; i < 9; ++i) f[i] = ST::ldf(P + plane_slot(opp(i)) * np + nb[opp(i)], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + (8 + opp(i)) * np + nb[opp(i)], d);
+        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + plane_slot(8 + opp(i)) * np + nb[opp(i)], d);
     }
 }
 
@@ -407,7 +407,7 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     const bool write = !OBS || (mode & OBS_WRITE);
 
     // ---- stream (AA write pattern) with link-wise boundary rules ----------
-    if (write) ST::stf(P + c, fs[0].v, d);
+    if (write) ST::stf(P + plane_slot(0) * np + c, fs[0].v, d);
     double q_in = 0.0, q_out = 0.0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -457,8 +457,8 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;  // even+stream or odd+boundary
-            if (to_own) ST::stf(P + opp(i) * np + c, v.v, d);
-            else ST::stf(P + i * np + nb[i], v.v, d);
+            if (to_own) ST::stf(P + plane_slot(opp(i)) * np + c, v.v, d);
+            else ST::stf(P + plane_slot(i) * np + nb[i], v.v, d);
         }
     }
 #pragma unroll
@@ -475,8 +475,8 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;
-            if (to_own) ST::stT(P + (8 + opp(i)) * np + c, v.v, d);
-            else ST::stT(P + (8 + i) * np + nb[i], v.v, d);
+            if (to_own) ST::stT(P + plane_slot(8 + opp(i)) * np + c, v.v, d);
+            else ST::stT(P + plane_slot(8 + i) * np + nb[i], v.v, d);
         }
     }
     if (OBS && (mode & OBS_STATS)) {
@@ -584,18 +584,18 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
     // ---- store --------------------------------------------------------------
     if (PAR == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
+        for (int q = 0; q < 9; ++q) ST::stf2(P + plane_slot(opp(q)) * np + row + x, a[q], b[q], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + plane_slot(8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
     } else {
-        ST::stf2(P + row + x, a[0], b[0], d);
+        ST::stf2(P + plane_slot(0) * np + row + x, a[0], b[0], d);
 #pragma unroll
         for (int k = 1; k < 13; ++k) {
             const bool heat = k > 8;
             const int i = heat ? k - 8 : k;
             const int pl = heat ? 8 + i : i;           // f*_i(x) goes to slot (x + e_i, i)
             const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
-            T* dst = P + pl * np + dr;
+            T* dst = P + plane_slot(pl) * np + dr;
             if (ex(i) == 0) {
                 if (heat) ST::stT2(dst + x, a[k], b[k], d);
                 else ST::stf2(dst + x, a[k], b[k], d);
@@ -715,19 +715,19 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
     if (PAR == 0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const float2 v = ST::ldf2(P + q * np + row + x, d);
+            const float2 v = ST::ldf2(P + plane_slot(q) * np + row + x, d);
             a[q] = v.x;
             b[q] = v.y;
         }
 #pragma unroll
         for (int i = 1; i <= 4; ++i) {
-            const float2 v = ST::ldT2(P + (8 + i) * np + row + x, d);
+            const float2 v = ST::ldT2(P + plane_slot(8 + i) * np + row + x, d);
             a[8 + i] = v.x;
             b[8 + i] = v.y;
         }
     } else {
         {
-            const float2 v = ST::ldf2(P + row + x, d);
+            const float2 v = ST::ldf2(P + plane_slot(0) * np + row + x, d);
             a[0] = v.x;
             b[0] = v.y;
         }
@@ -737,7 +737,7 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
             const int i = heat ? k - 8 : k;            // lattice direction
             const int pl = heat ? 8 + opp(i) : opp(i); // f_i(x) sits in slot (x - e_i, opp(i))
             const int sr = ey(i) == 1 ? rowd : (ey(i) == -1 ? rowu : row);
-            const T* src = P + pl * np + sr;
+            const T* src = P + plane_slot(pl) * np + sr;
             const float2 v = heat ? ST::ldT2(src + x, d) : ST::ldf2(src + x, d);
             if (ex(i) == 0) {
                 a[k] = v.x;
@@ -806,134 +806,110 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
 }
 
 // ---------------------------------------------------------------------------
-// Staged step of the FP32-arithmetic kernels (selected by launch shapes with
-// one row of threads per block).  A block of NT threads walks a strip of
-// W = 2 NT cells x H rows, one row at a time.  The 13 population segments each
-// row needs (own slots on an even step; on an odd step the source row of each
-// plane, widened by a 16-byte halo on both sides for the x-shifted links) are
-// copied into shared memory by bulk copies, several rows ahead of the row being
-// computed, so no register holds a pending load.  Each thread then updates a
-// cell pair from shared memory (interior pairs with collide_interior, every
-// other active cell with cell_body) and stores to global memory in the AA
-// pattern.  Rows never share a slot (each slot is read and written only by the
-// cell that owns it), so staging later rows before this row's stores land is
-// exact.  Halo elements that belong to cells of a neighbouring strip are copied
-// but never used.  Measured slower than the direct kernel on the eye
-// workloads; kept as an autotuner candidate.
+// Staged step of the FP32-arithmetic kernels (launch shapes with one row of
+// threads per block and tiles at least 64 cells wide): every warp runs its
+// own copy pipeline through shared memory.
+//
+// The unit of work is a row segment: 64 cells of one row of a tile (32 cell
+// pairs, one per lane).  The segments of the block's tiles (blockIdx.x,
+// + gridDim.x, ...) are numbered tile by tile, row by row; warp w takes
+// segments w, w + WS_WARPS, w + 2 WS_WARPS, ...  Each warp keeps WS_DEPTH
+// shared-memory stages.  For a segment it stages what the segment's cells
+// read with bulk tensor copies (cp.async.bulk.tensor) that complete on the
+// stage's barrier: on an even step the cells' own 13 slots (one copy), on an
+// odd step the three slot groups of the x-shifted links' sources, each from
+// its own row y + ey and widened by a 16-byte halo on both sides (three
+// copies; the slots are stored grouped by ey for this), and for tiles that
+// are not pure the mask row.  It then waits for its oldest stage, updates
+// that segment's pairs from shared memory, stores them in the AA pattern to
+// global memory, and refills the stage with the segment WS_DEPTH ahead.  So
+// WS_DEPTH segments per warp are in flight while it computes, no register
+// waits on a load, and a warp held up by boundary cells delays only itself.
+//
+// Each slot is read and written in a step only by the cell that owns it, so
+// staging later segments before earlier segments' stores land is exact; halo
+// and out-of-grid elements are copied (or zero-filled) but never used.
+// Whole-warp interior segments take the pair path's collision and stores;
+// other active cells take cell_body with the staged populations; pairs at a
+// periodic edge (whose wrap-around column is not staged) and instances whose
+// rows are not 16-byte aligned take the direct path.  Every barrier wait is
+// bounded: an expired wait sets the device status word, the warp waits
+// (bounded) for the copies it may still have in flight and leaves, and the
+// host reports the error instead of hanging.
 
-// elements per 16-byte chunk, and shared-memory segment length per plane
-template <class T>
-__host__ __device__ constexpr int chunk_elems() { return 16 / (int)sizeof(T); }
-template <class T>
-__host__ __device__ constexpr int seg_elems(int W) { return W + 2 * chunk_elems<T>(); }
-
-// source row of plane p for target row y on an odd step: f_i(x) sits in slot
-// (x - e_i, opp(i)), i.e. plane p = opp(i) holds it at row y - ey(i) = y + ey(p)
-__device__ __forceinline__ constexpr int plane_dir(int p) { return p < 9 ? p : p - 8; }
-
-template <class ST, int PAR>
-__device__ __forceinline__ void staged_row(const InstDesc& sd, const typename ST::T* stage, int x0,
-                                           int W, int y) {
-    using T = typename ST::T;
-    using R = float;
-    constexpr int CHE = chunk_elems<T>();
-    const int SEG = W + 2 * CHE;
-    const int nx = sd.nx;
-    const int x = x0 + 2 * (int)threadIdx.x;
-    if (x >= nx) return;
-    const uint32_t m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * nx + x);
-    if ((m2 & 7u) > POROUS && ((m2 >> 8) & 7u) > POROUS) return;  // neither cell is active
-    // the pair's wrap-around columns at a periodic edge are not staged: use
-    // the direct path there
-    if (x == 0 || x + 2 >= nx) {
-        update_cell<ST, false, PAR>(sd, x, y, 0, nullptr);
-        if (x + 1 < nx) update_cell<ST, false, PAR>(sd, x + 1, y, 0, nullptr);
-        return;
-    }
-    const int j = x - x0 + CHE;  // stage column of cell x
-    float a[13], b[13];
-#pragma unroll
-    for (int k = 0; k < 13; ++k) {
-        const bool heat = k > 8;
-        const int i = heat ? k - 8 : k;
-        const int pl = PAR == 0 ? k : (heat ? 8 + opp(i) : opp(i));
-        const int jj = PAR == 0 ? j : j - ex(i);
-        const T* src = stage + pl * SEG + jj;
-        if (heat) {
-            a[k] = ST::sldT(src, sd);
-            b[k] = ST::sldT(src + 1, sd);
-        } else {
-            a[k] = ST::sldf(src, sd);
-            b[k] = ST::sldf(src + 1, sd);
-        }
-    }
-    const bool interior = (m2 & 0x0E0Eu) == 0u;
-    if (!interior) {
-        // at least one cell next to a boundary (or solid): general update of
-        // each active cell with the staged populations
-        for (int v = 0; v < 2; ++v) {
-            const float* c = v == 0 ? a : b;
-            R f[9], g[4];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = c[i];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) g[i] = c[9 + i];
-            cell_body<ST, false, PAR>(sd, x + v, y, f, g, (uint8_t)(m2 >> (8 * v)), 0, nullptr);
-        }
-        return;
-    }
-    collide_interior(a, (m2 & 1u) != 0 && sd.tm_model == 0, sd.pf);
-    collide_interior(b, (m2 & 0x100u) != 0 && sd.tm_model == 0, sd.pf);
-    T* const P = static_cast<T*>(sd.pops);
-    const int np = (int)sd.npad;
-    const int ny = sd.ny;
-    const int row = y * nx;
-    const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
-    const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
-    if (PAR == 0) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], sd);
-#pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], sd);
-    } else {
-        ST::stf2(P + row + x, a[0], b[0], sd);
-#pragma unroll
-        for (int k = 1; k < 13; ++k) {
-            const bool heat = k > 8;
-            const int i = heat ? k - 8 : k;
-            const int pl = heat ? 8 + i : i;  // f*_i(x) goes to slot (x + e_i, i)
-            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
-            T* dst = P + pl * np + dr + x;
-            if (ex(i) == 0) {
-                if (heat) ST::stT2(dst, a[k], b[k], sd);
-                else ST::stf2(dst, a[k], b[k], sd);
-            } else {
-                const int o = ex(i);
-                if (heat) {
-                    ST::stT(dst + o, a[k], sd);
-                    ST::stT(dst + 1 + o, b[k], sd);
-                } else {
-                    ST::stf(dst + o, a[k], sd);
-                    ST::stf(dst + 1 + o, b[k], sd);
-                }
-            }
-        }
-    }
-}
-
-// One thread issues the 13 row segments of a row as bulk copies
-// (cp.async.bulk) that complete on the row's shared-memory barrier; TSTAGES
-// rows are in flight per block.  Every wait on a barrier is
-// bounded: if a copy has not landed after TMA_WAIT_LIMIT polls the block sets
-// the device status word, waits (again bounded) for the copies it issued and
-// leaves, and the host reports the error instead of hanging.
-
-constexpr int TSTAGES = 4;
+#ifndef LBM_WS_WARPS
+#define LBM_WS_WARPS 8
+#endif
+#ifndef LBM_WS_DEPTH
+#define LBM_WS_DEPTH 3
+#endif
+#ifndef LBM_WS_MINB
+#define LBM_WS_MINB 2
+#endif
+constexpr int WS_SEG = 64;               // cells per segment (32 pairs: one warp)
+constexpr int WS_WARPS = LBM_WS_WARPS;   // warps per block
+constexpr int WS_DEPTH = LBM_WS_DEPTH;   // stages per warp
+constexpr int WS_THREADS = 32 * WS_WARPS;
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
 
-// Non-zero after a staged copy failed to complete; read and cleared by the host
+// elements per 16-byte chunk
+template <class T>
+__host__ __device__ constexpr int chunk_elems() { return 16 / (int)sizeof(T); }
+
+// Stage layout, in elements of T from the stage base (128-byte aligned, as
+// bulk tensor copies need).  Even step: slot s's 64 cells at s * 64.  Odd
+// step: the three slot groups at 128-byte aligned bases, each slot row
+// ws_odd_pe elements long (the segment and a 16-byte chunk of halo on both
+// sides).  The mask row follows the odd layout.
+__host__ __device__ constexpr int ws_align128(int b) { return (b + 127) / 128 * 128; }
+template <class T>
+__host__ __device__ constexpr int ws_odd_pe() { return WS_SEG + 2 * chunk_elems<T>(); }
+template <class T>
+__host__ __device__ constexpr int ws_group_bytes(int g) {
+    return slot_group_size(g) * ws_odd_pe<T>() * (int)sizeof(T);
+}
+template <class T>
+__host__ __device__ constexpr int ws_group_base(int g) {  // bytes
+    return g == 0 ? 0
+                  : (g == 1 ? ws_align128(ws_group_bytes<T>(0))
+                            : ws_align128(ws_group_bytes<T>(0)) + ws_align128(ws_group_bytes<T>(1)));
+}
+template <class T>
+__host__ __device__ constexpr int ws_mask_off() { return ws_group_base<T>(2) + ws_group_bytes<T>(2); }
+template <class T>
+__host__ __device__ constexpr int ws_stage_bytes() { return ws_align128(ws_mask_off<T>() + WS_SEG); }
+// dynamic shared memory of a block (and room to align the ring)
+template <class T>
+__host__ __device__ constexpr int ws_smem_bytes() { return WS_WARPS * WS_DEPTH * ws_stage_bytes<T>() + 128; }
+// element offset of slot s's row in a stage
+template <class T, int PAR>
+__host__ __device__ constexpr int ws_slot_off(int s) {
+    return PAR == 0 ? s * WS_SEG
+                    : ws_group_base<T>(slot_group(s)) / (int)sizeof(T) +
+                          (s - slot_group_start(slot_group(s))) * ws_odd_pe<T>();
+}
+static_assert(ws_group_base<float>(1) % (int)sizeof(float) == 0 &&
+                  ws_group_base<__half>(2) % (int)sizeof(__half) == 0 &&
+                  13 * WS_SEG * (int)sizeof(float) <= ws_mask_off<float>() &&
+                  13 * WS_SEG * (int)sizeof(__half) <= ws_mask_off<__half>(),
+              "stage layout");
+
+// What a stage holds, written by the producer before it arrives on the
+// stage's full barrier.
+struct WsMeta {
+    int inst, flags, x, y;  // instance, WS_* flags, segment origin
+};
+enum : int {
+    WS_PURE = 1,    // pure tile: every cell an interior fluid cell, no mask needed
+    WS_MASK = 2,    // the mask row is staged after the planes
+    WS_DIRECT = 4,  // nothing staged: the warp takes the direct path
+    WS_SKIP = 8,    // segment outside the grid: nothing to do
+    WS_END = 16     // no more segments for this warp
+};
+
+// Non-zero after a staged wait expired; read and cleared by the host
 // (take_step_status).  Only the FP32-arithmetic unit instantiates the staged
-// kernels, so its copy of this word is the one that is used.
+// kernel, so its copy of this word is the one that is used.
 static __device__ int g_step_status = 0;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -941,6 +917,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -968,112 +947,319 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// Issue row y of a strip (global row sequence g) into stage g % TSTAGES.
-// Every copy starts on a 16-byte boundary and moves a multiple of 16 bytes:
-// x0 and W are multiples of the 16-byte chunk, so are nx (checked) and the
-// plane stride.
+// source row of plane p for target row y on an odd step: f_i(x) sits in slot
+// (x - e_i, opp(i)), i.e. plane p = opp(i) holds it at row y - ey(i) = y + ey(p)
+__device__ __forceinline__ constexpr int plane_dir(int p) { return p < 9 ? p : p - 8; }
+
+// Populations of the cell pair at segment column c (cells c, c + 1): own
+// slots on an even step, the x-shifted links' sources on an odd step.
+template <class ST, int PAR>
+__device__ __forceinline__ void ws_load(const InstDesc& d, const typename ST::T* stage, int c, float* a,
+                                        float* b) {
+    using T = typename ST::T;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        const bool heat = k > 8;
+        const int i = heat ? k - 8 : k;
+        const int pl = PAR == 0 ? k : (heat ? 8 + opp(i) : opp(i));
+        const int col = PAR == 0 ? c : c + chunk_elems<T>() - ex(i);
+        const T* src = stage + ws_slot_off<T, PAR>(plane_slot(pl)) + col;
+        a[k] = heat ? ST::sldT(src, d) : ST::sldf(src, d);
+        b[k] = heat ? ST::sldT(src + 1, d) : ST::sldf(src + 1, d);
+    }
+}
+
+// AA-pattern stores of a collided interior pair by one lane on its own (no
+// shuffles: the lanes of a warp need not all take this path).
+template <class ST, int PAR>
+__device__ __forceinline__ void pair_store_lane(const InstDesc& d, int x, int y, const float* a,
+                                                const float* b) {
+    using T = typename ST::T;
+    T* const P = static_cast<T*>(d.pops);
+    const int np = (int)d.npad;
+    const int nx = d.nx, ny = d.ny;
+    const int row = y * nx;
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ST::stf2(P + plane_slot(opp(q)) * np + row + x, a[q], b[q], d);
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + plane_slot(8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+    } else {
+        const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
+        const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
+        ST::stf2(P + plane_slot(0) * np + row + x, a[0], b[0], d);
+#pragma unroll
+        for (int k = 1; k < 13; ++k) {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;
+            const int pl = heat ? 8 + i : i;  // f*_i(x) goes to slot (x + e_i, i)
+            const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
+            T* dst = P + plane_slot(pl) * np + dr + x;
+            if (ex(i) == 0) {
+                if (heat) ST::stT2(dst, a[k], b[k], d);
+                else ST::stf2(dst, a[k], b[k], d);
+            } else {
+                const int o = ex(i);
+                if (heat) {
+                    ST::stT(dst + o, a[k], d);
+                    ST::stT(dst + 1 + o, b[k], d);
+                } else {
+                    ST::stf(dst + o, a[k], d);
+                    ST::stf(dst + 1 + o, b[k], d);
+                }
+            }
+        }
+    }
+}
+
+// One warp's staged segment: lane l updates cells x = m.x + 2 l, x + 1.
+template <class ST, int PAR>
+__device__ __forceinline__ void ws_segment(const InstDesc& d, const typename ST::T* stage,
+                                           const unsigned char* smask, const WsMeta& m) {
+    const int lane = threadIdx.x & 31;
+    const int nx = d.nx;
+    const int c = 2 * lane;  // column of cell x in the segment
+    const int x = m.x + c, y = m.y;
+    if (m.flags & WS_DIRECT) {
+        if (x < nx) update_cell<ST, false, PAR>(d, x, y, 0, nullptr);
+        if (x + 1 < nx) update_cell<ST, false, PAR>(d, x + 1, y, 0, nullptr);
+        return;
+    }
+    // a staged instance has nx a multiple of the 16-byte chunk, hence even:
+    // x < nx implies x + 1 < nx
+    const bool in = x < nx;
+    uint32_t m2 = 0xFFFFu;
+    if (m.flags & WS_PURE) m2 = 0u;
+    else if (in)
+        m2 = (m.flags & WS_MASK) ? *reinterpret_cast<const uint16_t*>(smask + c)
+                                 : *reinterpret_cast<const uint16_t*>(d.mask + (int64_t)y * nx + x);
+    const bool edge = x == 0 || x + 2 >= nx;
+    // both cells fluid or porous (type bits 1-2 clear), not next to a boundary (bit 3)
+    const bool interior = in && !edge && (m2 & 0x0E0Eu) == 0u;
+    const bool por0 = (m2 & 1u) != 0 && d.tm_model == 0;
+    const bool por1 = (m2 & 0x100u) != 0 && d.tm_model == 0;
+    float a[13], b[13];
+    if (__all_sync(0xffffffffu, interior)) {
+        ws_load<ST, PAR>(d, stage, c, a, b);
+        pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
+        return;
+    }
+    if (!in) return;
+    if ((m2 & TYPE_BITS) > POROUS && ((m2 >> 8) & TYPE_BITS) > POROUS) return;  // neither cell active
+    if (edge) {
+        update_cell<ST, false, PAR>(d, x, y, 0, nullptr);
+        update_cell<ST, false, PAR>(d, x + 1, y, 0, nullptr);
+        return;
+    }
+    ws_load<ST, PAR>(d, stage, c, a, b);
+    if (interior) {
+        collide_interior(a, por0, d.pf);
+        collide_interior(b, por1, d.pf);
+        pair_store_lane<ST, PAR>(d, x, y, a, b);
+        return;
+    }
+    // at least one cell next to a boundary: general update of each cell
+#pragma unroll 1
+    for (int v = 0; v < 2; ++v) {
+        const float* c = v == 0 ? a : b;
+        float f[9], g[4];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = c[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g[i] = c[9 + i];
+        cell_body<ST, false, PAR>(d, x + v, y, f, g, (uint8_t)(m2 >> (8 * v)), 0, nullptr);
+    }
+}
+
+__device__ __forceinline__ void warp_copy_desc(InstDesc* dst, const InstDesc* src) {
+    const uint64_t* s = reinterpret_cast<const uint64_t*>(src);
+    uint64_t* o = reinterpret_cast<uint64_t*>(dst);
+    __syncwarp();
+    for (int k = threadIdx.x & 31; k < (int)(sizeof(InstDesc) / 8); k += 32) o[k] = s[k];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void bulk_tensor_load(void* dst, const void* map, int x, int y, int z,
+                                                 uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];\n" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Posts one segment (or the end marker) into stage `st` of the calling warp,
+// completing on barrier `bar`.  te is the segment's tile entry (read ahead by
+// the caller), r and sx its row and segment in the tile; idesc holds the
+// descriptor of the instance last posted (refreshed here when it changes).
+// With the instance's tensor maps an even step takes one bulk tensor copy
+// (64 x 1 x 13 slots at row y) and an odd step three (one per slot group, at
+// row y + ey of the group, from 16 bytes left of the segment); odd steps on a
+// periodic row edge, and instances without maps, copy plane rows one slot at
+// a time.  Lane 13 copies the mask row of a tile that is not pure.
 template <class ST>
-__device__ __forceinline__ void tma_issue(const InstDesc& sd, typename ST::T* buf, uint64_t* bars,
-                                          uint32_t g, int x0, int W, int y, int parity) {
+__device__ __forceinline__ void ws_post(const InstDesc* __restrict__ insts, InstDesc& idesc, int& iheld,
+                                        const int4& te, bool valid, int r, int sx, int flip,
+                                        unsigned char* st, WsMeta& meta, uint64_t* bar) {
     using T = typename ST::T;
     constexpr int CHE = chunk_elems<T>();
-    const int SEG = W + 2 * CHE;
-    const int s = (int)(g % TSTAGES);
-    T* stage = buf + (size_t)s * 13 * SEG;
-    const int lo = parity ? max(x0 - CHE, 0) : x0;
-    const int hi = parity ? min(x0 + W + CHE, sd.nx) : min(x0 + W, sd.nx);
-    const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)sizeof(T);
-    const T* P = static_cast<const T*>(sd.pops);
-    const int np = (int)sd.npad;
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(&bars[s], 13u * bytes);
-    for (int p = 0; p < 13; ++p) {
-        int row = y;
-        if (parity) {
-            row = y + ey(plane_dir(p));
-            if (row < 0) row += sd.ny;
-            if (row >= sd.ny) row -= sd.ny;
+    constexpr int ES = (int)sizeof(T);
+    constexpr int PE = ws_odd_pe<T>();
+    const int lane = threadIdx.x & 31;
+    if (!valid) {
+        if (lane == 0) {
+            meta = WsMeta{-1, WS_END, 0, 0};
+            mbar_arrive(bar);
         }
-        bulk_load(stage + p * SEG + (lo - (x0 - CHE)), P + p * np + row * sd.nx + lo, bytes, &bars[s]);
+        return;
+    }
+    if (te.x != iheld) {
+        warp_copy_desc(&idesc, insts + te.x);
+        iheld = te.x;
+    }
+    const int nx = idesc.nx, ny = idesc.ny;
+    const int y = te.w + r, xs = te.z + sx * WS_SEG;
+    if (y >= ny || xs >= nx) {
+        if (lane == 0) {
+            meta = WsMeta{te.x, WS_SKIP, xs, y};
+            mbar_arrive(bar);
+        }
+        return;
+    }
+    const bool staged = (nx % CHE) == 0;  // plane rows start on 16-byte boundaries
+    const bool pure = (te.y & TILE_PURE) != 0;
+    const bool smask = !pure && (nx % 16) == 0;
+    if (!staged) {
+        if (lane == 0) {
+            meta = WsMeta{te.x, WS_DIRECT, xs, y};
+            mbar_arrive(bar);
+        }
+        return;
+    }
+    const int parity = (idesc.parity ^ flip) & 1;
+    const uint32_t mbytes = smask ? (uint32_t)min(WS_SEG, nx - xs) : 0u;
+    const unsigned char* maps = static_cast<const unsigned char*>(idesc.tmap);
+    const bool tensor = maps != nullptr && (parity == 0 || (y >= 1 && y <= ny - 2));
+    // row pieces of the one-slot-at-a-time copies
+    const int lo = parity ? max(xs - CHE, 0) : xs;
+    const int hi = parity ? min(xs + WS_SEG + CHE, nx) : min(xs + WS_SEG, nx);
+    const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)ES;
+    const uint32_t total = tensor ? (uint32_t)(13 * (parity ? PE : WS_SEG) * ES) + mbytes : 13u * bytes + mbytes;
+    if (lane == 0) {
+        meta = WsMeta{te.x, (pure ? WS_PURE : 0) | (smask ? WS_MASK : 0), xs, y};
+        mbar_expect_tx(bar, total);
+    }
+    __syncwarp();
+    T* const stage = reinterpret_cast<T*>(st);
+    if (tensor) {
+        if (parity == 0) {
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                bulk_tensor_load(stage, maps, xs, y, 0, bar);
+            }
+        } else if (lane < 3) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // map 1: 5-slot boxes (group 0), map 2: 4-slot boxes (groups 1, 2)
+            bulk_tensor_load(st + ws_group_base<T>(lane), maps + (lane == 0 ? 1 : 2) * 128, xs - CHE,
+                             y + slot_group_ey(lane), slot_group_start(lane), bar);
+        }
+    } else if (lane < 13) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const T* P = static_cast<const T*>(idesc.pops);
+        int row = y;
+        T* dst = stage + ws_slot_off<T, 0>(lane);
+        if (parity) {
+            row = y + slot_group_ey(slot_group(lane));
+            if (row < 0) row += ny;
+            if (row >= ny) row -= ny;
+            dst = stage + ws_slot_off<T, 1>(lane) + (lo - (xs - CHE));
+        }
+        bulk_load(dst, P + lane * idesc.npad + (int64_t)row * nx + lo, bytes, bar);
+    }
+    if (lane == 13 && mbytes != 0u) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bulk_load(st + ws_mask_off<T>(), idesc.mask + (int64_t)y * nx + xs, mbytes, bar);
     }
 }
 
 template <class ST>
-__global__ void __launch_bounds__(128) step_kernel_tma(const InstDesc* __restrict__ insts,
-                                                       const int4* __restrict__ tiles, int ntiles,
-                                                       int flip, int mode, Shape shape) {
+__global__ void __launch_bounds__(WS_THREADS, LBM_WS_MINB) step_kernel_ws(const InstDesc* __restrict__ insts,
+                                                                         const int4* __restrict__ tiles,
+                                                                         int ntiles, int flip, int mode,
+                                                                         Shape shape) {
     using T = typename ST::T;
-    extern __shared__ __align__(128) unsigned char tma_smem[];
-    __shared__ __align__(16) InstDesc sd;
-    __shared__ __align__(8) uint64_t bars[TSTAGES];
-    T* const buf = reinterpret_cast<T*>(tma_smem);
-    const int W = 2 * (int)blockDim.x;
-    const int SEG = seg_elems<T>(W);
-    const int H = shape.rpt;
+    constexpr int SB = ws_stage_bytes<T>();
+    constexpr uint32_t D = WS_DEPTH;
+    extern __shared__ __align__(128) unsigned char ws_smem[];
+    __shared__ __align__(16) InstDesc cdesc[WS_WARPS], idesc[WS_WARPS];
+    __shared__ __align__(16) WsMeta meta[WS_WARPS][WS_DEPTH];
+    __shared__ __align__(8) uint64_t bars[WS_WARPS][WS_DEPTH];
     (void)mode;
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < TSTAGES; ++k) mbar_init(&bars[k], 1);
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    // stages start on 128-byte boundaries (bulk tensor copy destinations)
+    unsigned char* const ring =
+        ws_smem + ((128u - (smem_addr(ws_smem) & 127u)) & 127u) + (size_t)warp * D * SB;
+    uint64_t* const bar = bars[warp];
+    if (lane == 0) {
+        for (uint32_t k = 0; k < D; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    __syncthreads();
-    // programmatic dependent launch (graph replays): nothing is read before
-    // the previous step has completed
+    __syncwarp();
+    // programmatic dependent launch (graph replays): let the next step launch,
+    // and wait for the previous one before the first copy
     grid_dependents_go();
     grid_dependency_wait();
-    uint32_t seq = 0;  // rows this block has staged so far (same in every thread)
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 te = tiles[t];
-        __syncthreads();
-        {
-            const uint64_t* src = reinterpret_cast<const uint64_t*>(insts + te.x);
-            uint64_t* dst = reinterpret_cast<uint64_t*>(&sd);
-            for (int k = threadIdx.x; k < (int)(sizeof(InstDesc) / 8); k += blockDim.x) dst[k] = src[k];
-        }
-        __syncthreads();
-        const int parity = (sd.parity ^ flip) & 1;
-        const int x0 = te.z, y0 = te.w;
-        const int rows = min(H, sd.ny - y0);
-        if ((sd.nx % chunk_elems<T>()) != 0) {
-            for (int r = 0; r < rows; ++r) {
-                const int x = x0 + 2 * (int)threadIdx.x;
-                for (int v = 0; v < 2; ++v)
-                    if (x + v < sd.nx) {
-                        if (parity) update_cell<ST, false, 1>(sd, x + v, y0 + r, 0, nullptr);
-                        else update_cell<ST, false, 0>(sd, x + v, y0 + r, 0, nullptr);
-                    }
-            }
-            continue;
-        }
-        const uint32_t base = seq;
-        int issued = 0;  // rows of this strip issued so far (meaningful in thread 0)
-        if (threadIdx.x == 0)
-            for (; issued < TSTAGES - 1 && issued < rows; ++issued)
-                tma_issue<ST>(sd, buf, bars, base + issued, x0, W, y0 + issued, parity);
-        for (int r = 0; r < rows; ++r) {
-            if (threadIdx.x == 0 && issued < rows && issued < r + TSTAGES) {
-                tma_issue<ST>(sd, buf, bars, base + issued, x0, W, y0 + issued, parity);
-                ++issued;
-            }
-            const uint32_t g = base + r;
-            const bool ok = mbar_wait_bounded(&bars[g % TSTAGES], (g / TSTAGES) & 1u);
-            if (__syncthreads_or(!ok)) {
-                // a copy did not land: record it, wait (bounded) for what this
-                // block still has in flight, and leave
-                if (threadIdx.x == 0) {
-                    atomicExch(&g_step_status, 1);
-                    for (int q = r; q < issued; ++q) {
-                        const uint32_t gq = base + q;
-                        (void)mbar_wait_bounded(&bars[gq % TSTAGES], (gq / TSTAGES) & 1u);
-                    }
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+
+    // segment numbering: item i -> tile ordinal i / ipt, row, segment
+    const int nseg = shape.tw / WS_SEG;
+    const int ipt = shape.rpt * nseg;
+    auto tile_of = [&](int64_t i) -> int64_t { return (int64_t)blockIdx.x + (i / ipt) * (int64_t)gridDim.x; };
+    int iheld = -1, cheld = -1;
+    int64_t next = warp;  // next item to post
+    for (uint32_t k = 0; k < D; ++k, next += WS_WARPS) {
+        const int64_t t = tile_of(next);
+        const bool valid = t < ntiles;
+        const int4 te = valid ? tiles[t] : make_int4(0, 0, 0, 0);
+        const int rem = (int)(next % ipt);
+        ws_post<ST>(insts, idesc[warp], iheld, te, valid, rem / nseg, rem % nseg, flip, ring + k * SB,
+                    meta[warp][k], &bar[k]);
+    }
+    for (uint32_t j = 0;; ++j) {
+        const uint32_t s = j % D;
+        // tile entry of the segment posted after this one, read ahead
+        const int64_t tn = tile_of(next);
+        const bool vn = tn < ntiles;
+        int4 ten = make_int4(0, 0, 0, 0);
+        if (vn) ten = tiles[tn];
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (j / D) & 1u))) {
+            if (lane == 0) {
+                atomicExch(&g_step_status, 1);
+                for (uint32_t q = 1; q < D; ++q) {  // the other stages may still be in flight
+                    const uint32_t jq = j + q;
+                    (void)mbar_wait_bounded(&bar[jq % D], (jq / D) & 1u);
                 }
-                return;
             }
-            const T* stage = buf + (size_t)(g % TSTAGES) * 13 * SEG;
-            if (parity) staged_row<ST, 1>(sd, stage, x0, W, y0 + r);
-            else staged_row<ST, 0>(sd, stage, x0, W, y0 + r);
-            __syncthreads();
+            return;
         }
-        seq += rows;
+        const WsMeta m = meta[warp][s];
+        if (m.flags & WS_END) return;  // every later stage holds an end marker too
+        if (!(m.flags & WS_SKIP)) {
+            if (m.inst != cheld) {
+                warp_copy_desc(&cdesc[warp], insts + m.inst);
+                cheld = m.inst;
+            }
+            const unsigned char* st = ring + s * SB;
+            const T* stage = reinterpret_cast<const T*>(st);
+            const unsigned char* smk = st + ws_mask_off<T>();
+            if ((cdesc[warp].parity ^ flip) & 1) ws_segment<ST, 1>(cdesc[warp], stage, smk, m);
+            else ws_segment<ST, 0>(cdesc[warp], stage, smk, m);
+        }
+        __syncwarp();
+        const int rem = (int)(next % ipt);
+        ws_post<ST>(insts, idesc[warp], iheld, ten, vn, rem / nseg, rem % nseg, flip, ring + s * SB,
+                    meta[warp][s], &bar[s]);
+        next += WS_WARPS;
     }
 }
 

@@ -1,7 +1,10 @@
 // FP32-arithmetic instantiations of the fused step: FP32 storage and the two
-// 16-bit deviation storages (FP16 scaled, BF16).  Plain steps with one row of
-// threads per block take the TMA-staged kernel; observing steps and
-// other shapes take the direct kernel.
+// 16-bit deviation storages (FP16 scaled, BF16).  Plain steps of launch shapes
+// with one row of threads per block and tiles at least 64 cells wide take the
+// staged kernel (persistent: its grid is capped at the blocks the device
+// holds at once); observing steps and other shapes take the direct kernel.
+#include <algorithm>
+
 #include "kernel_body.cuh"
 
 namespace lbm {
@@ -9,18 +12,26 @@ namespace lbm {
 template <class ST>
 static StepPlan plan_t(bool obs, Shape shape) {
     StepPlan p;
-    if (!obs && shape.bh == 1) {
-        using T = typename ST::T;
-        p.func = reinterpret_cast<const void*>(&step_kernel_tma<ST>);
-        p.block = dim3(shape.tw / 2, 1);
-        p.smem = (size_t)TSTAGES * 13 * seg_elems<T>(shape.tw) * sizeof(T);
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(reinterpret_cast<const void*>(&step_kernel_tma<ST>),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)TSTAGES * 13 * seg_elems<T>(256) * sizeof(T)));
-            attr_set = true;
+    if (!obs && shape.bh == 1 && shape.tw >= WS_SEG) {
+        const void* f = reinterpret_cast<const void*>(&step_kernel_ws<ST>);
+        p.func = f;
+        p.block = dim3(WS_THREADS);
+        p.smem = (size_t)ws_smem_bytes<typename ST::T>();
+        // co-resident blocks, per device (set once per device and storage)
+        static int cap[64] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+        if (cap[dev] == 0) {
+            int per_sm = 0, sms = 0;
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) ==
+                    cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, WS_THREADS, p.smem) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+                cap[dev] = std::max(per_sm, 1) * std::max(sms, 1);
+            else
+                cap[dev] = -1;
         }
+        p.max_grid = cap[dev] > 0 ? cap[dev] : 1;
     } else {
         p.func = obs ? reinterpret_cast<const void*>(&step_kernel<ST, true>)
                      : reinterpret_cast<const void*>(&step_kernel<ST, false>);

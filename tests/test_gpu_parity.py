@@ -347,6 +347,33 @@ def test_eye_sixteen_bit_storage(prec, unit_roundoff):
     assert rel_err(dom, ref) <= 4.0 * unit_roundoff * n ** 0.5
 
 
+STAGED_SHAPES = [
+    dict(tile_w=64, block_rows=1, rows_per_thread=4, blocks_per_sm=0),
+    dict(tile_w=256, block_rows=1, rows_per_thread=2, blocks_per_sm=1),
+]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("nx,ny", [(160, 80), (200, 100), (150, 75)])
+@pytest.mark.parametrize("launch", range(len(STAGED_SHAPES)))
+def test_staged_kernel_eye(prec, nx, ny, launch):
+    """The warp-specialised staged kernel (one launch per step of a one-row
+    shape with tiles of whole 64-cell segments) on grids whose mask rows are
+    staged (nx a multiple of 16), read from global memory (nx = 200), or
+    whose rows are not staged at all (nx = 150: population rows off the
+    16-byte grid), after an odd and an even number of steps, against the FP64
+    oracle (16-bit storages: a few unit roundoffs times sqrt(n), as above)."""
+    dom, ref, _ = eye_pair(nx, ny, prec, launch=STAGED_SHAPES[launch])
+    u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}.get(prec)
+    done = 0
+    for n in (1, 40):
+        dom.step(n)
+        ref.run(n)
+        done += n
+        bound = tol("f32", done) if u is None else 4.0 * u * done ** 0.5
+        assert rel_err(dom, ref) <= bound, done
+
+
 def test_supine_eye_mirror_symmetry_fp32():
     """The supine eye without noise stays mirror-symmetric on the FP32 path
     (cell pairs, shuffled x-shifted links in both directions)."""
