@@ -206,15 +206,15 @@ __device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, type
     m = d.mask[c];
     if (PAR == 0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = ST::ldf(P + plane_slot(i) * np + c, d);
+        for (int i = 0; i < 9; ++i) f[i] = ST::ldf(P + i * np + c, d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + plane_slot(8 + i) * np + c, d);
+        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + (8 + i) * np + c, d);
     } else {
-        f[0] = ST::ldf(P + plane_slot(0) * np + c, d);
+        f[0] = ST::ldf(P + c, d);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = ST::ldf(P + plane_slot(opp(i)) * np + nb[opp(i)], d);
+        for (int i = 1; i < 9; ++i) f[i] = ST::ldf(P + opp(i) * np + nb[opp(i)], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + plane_slot(8 + opp(i)) * np + nb[opp(i)], d);
+        for (int i = 1; i <= 4; ++i) g[i - 1] = ST::ldT(P + (8 + opp(i)) * np + nb[opp(i)], d);
     }
 }
 
@@ -407,7 +407,7 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     const bool write = !OBS || (mode & OBS_WRITE);
 
     // ---- stream (AA write pattern) with link-wise boundary rules ----------
-    if (write) ST::stf(P + plane_slot(0) * np + c, fs[0].v, d);
+    if (write) ST::stf(P + c, fs[0].v, d);
     double q_in = 0.0, q_out = 0.0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -457,8 +457,8 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;  // even+stream or odd+boundary
-            if (to_own) ST::stf(P + plane_slot(opp(i)) * np + c, v.v, d);
-            else ST::stf(P + plane_slot(i) * np + nb[i], v.v, d);
+            if (to_own) ST::stf(P + opp(i) * np + c, v.v, d);
+            else ST::stf(P + i * np + nb[i], v.v, d);
         }
     }
 #pragma unroll
@@ -475,8 +475,8 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         }
         if (write) {
             const bool to_own = (PAR == 0) != is_bnd;
-            if (to_own) ST::stT(P + plane_slot(8 + opp(i)) * np + c, v.v, d);
-            else ST::stT(P + plane_slot(8 + i) * np + nb[i], v.v, d);
+            if (to_own) ST::stT(P + (8 + opp(i)) * np + c, v.v, d);
+            else ST::stT(P + (8 + i) * np + nb[i], v.v, d);
         }
     }
     if (OBS && (mode & OBS_STATS)) {
@@ -584,18 +584,18 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
     // ---- store --------------------------------------------------------------
     if (PAR == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + plane_slot(opp(q)) * np + row + x, a[q], b[q], d);
+        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + plane_slot(8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
     } else {
-        ST::stf2(P + plane_slot(0) * np + row + x, a[0], b[0], d);
+        ST::stf2(P + row + x, a[0], b[0], d);
 #pragma unroll
         for (int k = 1; k < 13; ++k) {
             const bool heat = k > 8;
             const int i = heat ? k - 8 : k;
             const int pl = heat ? 8 + i : i;           // f*_i(x) goes to slot (x + e_i, i)
             const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
-            T* dst = P + plane_slot(pl) * np + dr;
+            T* dst = P + pl * np + dr;
             if (ex(i) == 0) {
                 if (heat) ST::stT2(dst + x, a[k], b[k], d);
                 else ST::stf2(dst + x, a[k], b[k], d);
@@ -715,19 +715,19 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
     if (PAR == 0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const float2 v = ST::ldf2(P + plane_slot(q) * np + row + x, d);
+            const float2 v = ST::ldf2(P + q * np + row + x, d);
             a[q] = v.x;
             b[q] = v.y;
         }
 #pragma unroll
         for (int i = 1; i <= 4; ++i) {
-            const float2 v = ST::ldT2(P + plane_slot(8 + i) * np + row + x, d);
+            const float2 v = ST::ldT2(P + (8 + i) * np + row + x, d);
             a[8 + i] = v.x;
             b[8 + i] = v.y;
         }
     } else {
         {
-            const float2 v = ST::ldf2(P + plane_slot(0) * np + row + x, d);
+            const float2 v = ST::ldf2(P + row + x, d);
             a[0] = v.x;
             b[0] = v.y;
         }
@@ -737,7 +737,7 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
             const int i = heat ? k - 8 : k;            // lattice direction
             const int pl = heat ? 8 + opp(i) : opp(i); // f_i(x) sits in slot (x - e_i, opp(i))
             const int sr = ey(i) == 1 ? rowd : (ey(i) == -1 ? rowu : row);
-            const T* src = P + plane_slot(pl) * np + sr;
+            const T* src = P + pl * np + sr;
             const float2 v = heat ? ST::ldT2(src + x, d) : ST::ldf2(src + x, d);
             if (ex(i) == 0) {
                 a[k] = v.x;
@@ -815,12 +815,11 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
 // + gridDim.x, ...) are numbered tile by tile, row by row; warp w takes
 // segments w, w + WS_WARPS, w + 2 WS_WARPS, ...  Each warp keeps WS_DEPTH
 // shared-memory stages.  For a segment it stages what the segment's cells
-// read with bulk tensor copies (cp.async.bulk.tensor) that complete on the
-// stage's barrier: on an even step the cells' own 13 slots (one copy), on an
-// odd step the three slot groups of the x-shifted links' sources, each from
-// its own row y + ey and widened by a 16-byte halo on both sides (three
-// copies; the slots are stored grouped by ey for this), and for tiles that
-// are not pure the mask row.  It then waits for its oldest stage, updates
+// read with bulk copies that complete on the stage's barrier: on an even step
+// the cells' own slots of all 13 planes (one bulk tensor copy,
+// cp.async.bulk.tensor), on an odd step the x-shifted links' sources, plane p
+// from row y + ey(p) and widened by a 16-byte halo on both sides (one
+// cp.async.bulk per plane), and for tiles that are not pure the mask row.  It then waits for its oldest stage, updates
 // that segment's pairs from shared memory, stores them in the AA pattern to
 // global memory, and refills the stage with the segment WS_DEPTH ahead.  So
 // WS_DEPTH segments per warp are in flight while it computes, no register
@@ -857,42 +856,22 @@ template <class T>
 __host__ __device__ constexpr int chunk_elems() { return 16 / (int)sizeof(T); }
 
 // Stage layout, in elements of T from the stage base (128-byte aligned, as
-// bulk tensor copies need).  Even step: slot s's 64 cells at s * 64.  Odd
-// step: the three slot groups at 128-byte aligned bases, each slot row
-// ws_odd_pe elements long (the segment and a 16-byte chunk of halo on both
-// sides).  The mask row follows the odd layout.
+// bulk tensor copies need).  Even step: plane p's 64 cells at p * 64.  Odd
+// step: plane p's row piece at p * ws_odd_pe (the segment and a 16-byte chunk
+// of halo on both sides).  The mask row follows the odd layout.
 __host__ __device__ constexpr int ws_align128(int b) { return (b + 127) / 128 * 128; }
 template <class T>
 __host__ __device__ constexpr int ws_odd_pe() { return WS_SEG + 2 * chunk_elems<T>(); }
+template <class T, int PAR>
+__host__ __device__ constexpr int ws_plane_off(int p) { return p * (PAR == 0 ? WS_SEG : ws_odd_pe<T>()); }
 template <class T>
-__host__ __device__ constexpr int ws_group_bytes(int g) {
-    return slot_group_size(g) * ws_odd_pe<T>() * (int)sizeof(T);
-}
-template <class T>
-__host__ __device__ constexpr int ws_group_base(int g) {  // bytes
-    return g == 0 ? 0
-                  : (g == 1 ? ws_align128(ws_group_bytes<T>(0))
-                            : ws_align128(ws_group_bytes<T>(0)) + ws_align128(ws_group_bytes<T>(1)));
-}
-template <class T>
-__host__ __device__ constexpr int ws_mask_off() { return ws_group_base<T>(2) + ws_group_bytes<T>(2); }
+__host__ __device__ constexpr int ws_mask_off() { return 13 * ws_odd_pe<T>() * (int)sizeof(T); }
 template <class T>
 __host__ __device__ constexpr int ws_stage_bytes() { return ws_align128(ws_mask_off<T>() + WS_SEG); }
 // dynamic shared memory of a block (and room to align the ring)
 template <class T>
 __host__ __device__ constexpr int ws_smem_bytes() { return WS_WARPS * WS_DEPTH * ws_stage_bytes<T>() + 128; }
-// element offset of slot s's row in a stage
-template <class T, int PAR>
-__host__ __device__ constexpr int ws_slot_off(int s) {
-    return PAR == 0 ? s * WS_SEG
-                    : ws_group_base<T>(slot_group(s)) / (int)sizeof(T) +
-                          (s - slot_group_start(slot_group(s))) * ws_odd_pe<T>();
-}
-static_assert(ws_group_base<float>(1) % (int)sizeof(float) == 0 &&
-                  ws_group_base<__half>(2) % (int)sizeof(__half) == 0 &&
-                  13 * WS_SEG * (int)sizeof(float) <= ws_mask_off<float>() &&
-                  13 * WS_SEG * (int)sizeof(__half) <= ws_mask_off<__half>(),
-              "stage layout");
+static_assert(ws_mask_off<float>() % 16 == 0 && ws_mask_off<__half>() % 16 == 0, "stage layout");
 
 // What a stage holds, written by the producer before it arrives on the
 // stage's full barrier.
@@ -963,7 +942,7 @@ __device__ __forceinline__ void ws_load(const InstDesc& d, const typename ST::T*
         const int i = heat ? k - 8 : k;
         const int pl = PAR == 0 ? k : (heat ? 8 + opp(i) : opp(i));
         const int col = PAR == 0 ? c : c + chunk_elems<T>() - ex(i);
-        const T* src = stage + ws_slot_off<T, PAR>(plane_slot(pl)) + col;
+        const T* src = stage + ws_plane_off<T, PAR>(pl) + col;
         a[k] = heat ? ST::sldT(src, d) : ST::sldf(src, d);
         b[k] = heat ? ST::sldT(src + 1, d) : ST::sldf(src + 1, d);
     }
@@ -981,20 +960,20 @@ __device__ __forceinline__ void pair_store_lane(const InstDesc& d, int x, int y,
     const int row = y * nx;
     if (PAR == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + plane_slot(opp(q)) * np + row + x, a[q], b[q], d);
+        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + plane_slot(8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
     } else {
         const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
         const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
-        ST::stf2(P + plane_slot(0) * np + row + x, a[0], b[0], d);
+        ST::stf2(P + row + x, a[0], b[0], d);
 #pragma unroll
         for (int k = 1; k < 13; ++k) {
             const bool heat = k > 8;
             const int i = heat ? k - 8 : k;
             const int pl = heat ? 8 + i : i;  // f*_i(x) goes to slot (x + e_i, i)
             const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
-            T* dst = P + plane_slot(pl) * np + dr + x;
+            T* dst = P + pl * np + dr + x;
             if (ex(i) == 0) {
                 if (heat) ST::stT2(dst, a[k], b[k], d);
                 else ST::stf2(dst, a[k], b[k], d);
@@ -1092,11 +1071,11 @@ __device__ __forceinline__ void bulk_tensor_load(void* dst, const void* map, int
 // completing on barrier `bar`.  te is the segment's tile entry (read ahead by
 // the caller), r and sx its row and segment in the tile; idesc holds the
 // descriptor of the instance last posted (refreshed here when it changes).
-// With the instance's tensor maps an even step takes one bulk tensor copy
-// (64 x 1 x 13 slots at row y) and an odd step three (one per slot group, at
-// row y + ey of the group, from 16 bytes left of the segment); odd steps on a
-// periodic row edge, and instances without maps, copy plane rows one slot at
-// a time.  Lane 13 copies the mask row of a tile that is not pure.
+// On an even step every plane is read at row y, and with the instance's
+// tensor map one bulk tensor copy (64 x 1 x 13 planes) stages them all.  On
+// an odd step (or without a map) lanes 0-12 copy one plane's row piece each
+// (plane p from row y + ey(p), widened by a 16-byte halo on both sides).
+// Lane 13 copies the mask row of a tile that is not pure.
 template <class ST>
 __device__ __forceinline__ void ws_post(const InstDesc* __restrict__ insts, InstDesc& idesc, int& iheld,
                                         const int4& te, bool valid, int r, int sx, int flip,
@@ -1104,7 +1083,6 @@ __device__ __forceinline__ void ws_post(const InstDesc* __restrict__ insts, Inst
     using T = typename ST::T;
     constexpr int CHE = chunk_elems<T>();
     constexpr int ES = (int)sizeof(T);
-    constexpr int PE = ws_odd_pe<T>();
     const int lane = threadIdx.x & 31;
     if (!valid) {
         if (lane == 0) {
@@ -1138,13 +1116,12 @@ __device__ __forceinline__ void ws_post(const InstDesc* __restrict__ insts, Inst
     }
     const int parity = (idesc.parity ^ flip) & 1;
     const uint32_t mbytes = smask ? (uint32_t)min(WS_SEG, nx - xs) : 0u;
-    const unsigned char* maps = static_cast<const unsigned char*>(idesc.tmap);
-    const bool tensor = maps != nullptr && (parity == 0 || (y >= 1 && y <= ny - 2));
-    // row pieces of the one-slot-at-a-time copies
+    const bool tensor = parity == 0 && idesc.tmap != nullptr;
+    // row pieces of the one-plane-at-a-time copies
     const int lo = parity ? max(xs - CHE, 0) : xs;
     const int hi = parity ? min(xs + WS_SEG + CHE, nx) : min(xs + WS_SEG, nx);
     const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)ES;
-    const uint32_t total = tensor ? (uint32_t)(13 * (parity ? PE : WS_SEG) * ES) + mbytes : 13u * bytes + mbytes;
+    const uint32_t total = tensor ? (uint32_t)(13 * WS_SEG * ES) + mbytes : 13u * bytes + mbytes;
     if (lane == 0) {
         meta = WsMeta{te.x, (pure ? WS_PURE : 0) | (smask ? WS_MASK : 0), xs, y};
         mbar_expect_tx(bar, total);
@@ -1152,27 +1129,21 @@ __device__ __forceinline__ void ws_post(const InstDesc* __restrict__ insts, Inst
     __syncwarp();
     T* const stage = reinterpret_cast<T*>(st);
     if (tensor) {
-        if (parity == 0) {
-            if (lane == 0) {
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                bulk_tensor_load(stage, maps, xs, y, 0, bar);
-            }
-        } else if (lane < 3) {
+        if (lane == 0) {
+            // the warp's earlier reads of this stage precede the copy into it
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            // map 1: 5-slot boxes (group 0), map 2: 4-slot boxes (groups 1, 2)
-            bulk_tensor_load(st + ws_group_base<T>(lane), maps + (lane == 0 ? 1 : 2) * 128, xs - CHE,
-                             y + slot_group_ey(lane), slot_group_start(lane), bar);
+            bulk_tensor_load(stage, idesc.tmap, xs, y, 0, bar);
         }
     } else if (lane < 13) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         const T* P = static_cast<const T*>(idesc.pops);
         int row = y;
-        T* dst = stage + ws_slot_off<T, 0>(lane);
+        T* dst = stage + ws_plane_off<T, 0>(lane);
         if (parity) {
-            row = y + slot_group_ey(slot_group(lane));
+            row = y + ey(plane_dir(lane));
             if (row < 0) row += ny;
             if (row >= ny) row -= ny;
-            dst = stage + ws_slot_off<T, 1>(lane) + (lo - (xs - CHE));
+            dst = stage + ws_plane_off<T, 1>(lane) + (lo - (xs - CHE));
         }
         bulk_load(dst, P + lane * idesc.npad + (int64_t)row * nx + lo, bytes, bar);
     }

@@ -132,7 +132,7 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.partials = off; off = align_up(off + (size_t)L.max_tiles * NPART * sizeof(double));
     L.usnap = off; off = align_up(off + 2 * (size_t)L.npad * real_size(prec));
     L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
-    L.tmap = off; off = align_up(off + 3 * sizeof(CUtensorMap));
+    L.tmap = off; off = align_up(off + sizeof(CUtensorMap));
     L.total = off;
     return true;
 }
@@ -407,8 +407,8 @@ __global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, u
             noise = noise_amp * (2.0 * u01 - 1.0);
         }
         const double Ti = 0.25 * (d.pd.T0 + noise);
-        for (int i = 0; i < 9; ++i) ST::stf(P + plane_slot(i) * d.npad + c, (typename ST::R)feq[i], d);
-        for (int i = 1; i <= 4; ++i) ST::stT(P + plane_slot(8 + i) * d.npad + c, (typename ST::R)Ti, d);
+        for (int i = 0; i < 9; ++i) ST::stf(P + i * d.npad + c, (typename ST::R)feq[i], d);
+        for (int i = 1; i <= 4; ++i) ST::stT(P + (8 + i) * d.npad + c, (typename ST::R)Ti, d);
     }
 }
 
@@ -416,7 +416,7 @@ __global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, u
 __device__ __forceinline__ int64_t slot_of(const InstDesc& d, int x, int y, int i, int parity,
                                            bool heat) {
     const int64_t c = (int64_t)y * d.nx + x;
-    if (parity == 0 || i == 0) return plane_slot(heat ? 8 + i : i) * d.npad + c;
+    if (parity == 0 || i == 0) return (heat ? (8 + i) : i) * d.npad + c;
     // odd: f_i(x) sits in slot (x - e_i, opp(i))
     int xs = x - ex(i), ys = y - ey(i);
     if (xs < 0) xs += d.nx;
@@ -424,7 +424,7 @@ __device__ __forceinline__ int64_t slot_of(const InstDesc& d, int x, int y, int 
     if (ys < 0) ys += d.ny;
     if (ys >= d.ny) ys -= d.ny;
     const int o = opp(i);
-    return plane_slot(heat ? 8 + o : o) * d.npad + (int64_t)ys * d.nx + xs;
+    return (heat ? (8 + o) : o) * d.npad + (int64_t)ys * d.nx + xs;
 }
 
 template <class ST>
@@ -602,14 +602,12 @@ extern "C" size_t lbm_domain_bytes(const lbm_geometry_desc* desc, int32_t precis
     return L.total;
 }
 
-// Bulk tensor copy maps of the populations for the staged kernel: the 13
-// slots as a (x, y, slot) tensor of nx x ny x 13 elements.  Box 0 (64 x 1 x
-// 13) stages a segment's own slots on an even step; boxes 1 and 2 (64 cells
-// and a 16-byte chunk on both sides, 1 row, 5 and 4 slots) stage one slot
-// group of a segment's odd-step sources.  Out-of-grid box elements are
-// filled with zeros (they are never used).  Returns false where the driver
-// offers no encoder or the rows are not 16-byte aligned; the staged kernel
-// then copies row pieces one slot at a time.
+// Bulk tensor copy map of the populations for the staged kernel: the 13
+// planes as an nx x ny x 13 tensor, boxes of 64 x 1 x 13 (a row segment's
+// own slots on an even step; out-of-grid elements are filled with zeros and
+// never used).  Returns false where the driver offers no encoder or the rows
+// are not 16-byte aligned; the staged kernel then copies row pieces one
+// plane at a time.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -632,28 +630,21 @@ static EncodeTiledFn tensor_encoder() {
     return fn;
 }
 
-static bool encode_pop_maps(const lbm_domain* d, CUtensorMap* maps) {
+static bool encode_pop_map(const lbm_domain* d, CUtensorMap* map) {
     if (d->prec == LBM_F64) return false;
     const int es = (int)store_size(d->prec);
-    const int che = 16 / es;
-    if (d->nx % che != 0) return false;
+    if (d->nx % (16 / es) != 0) return false;
     const EncodeTiledFn enc = tensor_encoder();
     if (!enc) return false;
     const CUtensorMapDataType dt =
         d->prec == LBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     const cuuint64_t dims[3] = {(cuuint64_t)d->nx, (cuuint64_t)d->ny, 13};
     const cuuint64_t strides[2] = {(cuuint64_t)d->nx * es, (cuuint64_t)d->L.npad * es};
+    const cuuint32_t box[3] = {(cuuint32_t)WS_SEG, 1, 13};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint32_t wide = (cuuint32_t)(WS_SEG + 2 * che);
-    const cuuint32_t boxes[3][3] = {{(cuuint32_t)WS_SEG, 1, 13},
-                                    {wide, 1, (cuuint32_t)slot_group_size(0)},
-                                    {wide, 1, (cuuint32_t)slot_group_size(1)}};
-    for (int k = 0; k < 3; ++k)
-        if (enc(&maps[k], dt, 3, d->base + d->L.pops, dims, strides, boxes[k], estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return false;
-    return true;
+    return enc(map, dt, 3, d->base + d->L.pops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t precision,
@@ -738,10 +729,10 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
         delete d;
         return fail(LBM_ECUDA, "mask upload failed: %s", cudaGetErrorString(ce));
     }
-    CUtensorMap maps[3];
-    if (encode_pop_maps(d, maps)) {
+    CUtensorMap map;
+    if (encode_pop_map(d, &map)) {
         // pageable source: the copy has consumed it when the call returns
-        ce = cudaMemcpy(d->base + d->L.tmap, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        ce = cudaMemcpy(d->base + d->L.tmap, &map, sizeof(map), cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
             delete d;
             return fail(LBM_ECUDA, "tensor map upload failed: %s", cudaGetErrorString(ce));

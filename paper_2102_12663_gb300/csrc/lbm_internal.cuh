@@ -24,25 +24,6 @@ struct CurvedCell {
 };
 enum : int { FLUID = 0, POROUS = 1, COLD = 2, HOT = 3, ADIABATIC = 4, INLET = 5, OUTLET = 6 };
 
-// Memory slot of population plane p (0-8: f_0..f_8, 9-12: T_1..T_4).  On an
-// odd step plane p = opp(i) holds the source of link i in row y + ey(p) (the
-// AA pattern), so the planes are stored grouped by ey(p): slots 0-4 hold the
-// planes with ey = 0 (f_0, f_1, f_3, T_1, T_3), slots 5-8 those with ey = +1
-// (f_2, f_5, f_6, T_2) and slots 9-12 those with ey = -1 (f_4, f_7, f_8, T_4).
-// A row of cells then reads each group from one row of consecutive slots,
-// which one three-dimensional bulk tensor copy can stage.
-__host__ __device__ constexpr int plane_slot(int p) {
-    return p == 0 ? 0 : p == 1 ? 1 : p == 3 ? 2 : p == 9 ? 3 : p == 11 ? 4
-         : p == 2 ? 5 : p == 5 ? 6 : p == 6 ? 7 : p == 10 ? 8
-         : p == 4 ? 9 : p == 7 ? 10 : p == 8 ? 11 : 12;
-}
-// slot group of slot s (0: ey = 0, 1: ey = +1, 2: ey = -1), its first slot,
-// its size and its row offset
-__host__ __device__ constexpr int slot_group(int s) { return s < 5 ? 0 : (s < 9 ? 1 : 2); }
-__host__ __device__ constexpr int slot_group_start(int g) { return g == 0 ? 0 : (g == 1 ? 5 : 9); }
-__host__ __device__ constexpr int slot_group_size(int g) { return g == 0 ? 5 : 4; }
-__host__ __device__ constexpr int slot_group_ey(int g) { return g == 0 ? 0 : (g == 1 ? 1 : -1); }
-
 // Observation modes of the fused step (bit set).
 enum : int {
     OBS_STATS = 1,  // per-tile partial sums of the observables
@@ -101,12 +82,14 @@ struct InstDesc {
     int32_t bouzidi;     // interpolated bounce-back on the curved cornea
     const int32_t* qcol; // nx + 1 prefix sums into qtab (curved cells per column)
     const CurvedCell* qtab;
-    const void* tmap;    // 3 bulk-tensor copy maps of the populations (staged kernel), or null
     double arc_xc, arc_yc;
     Phys<double> pd;
     Phys<float> pf;
     // 16-bit storage: stored = (value - shift) * scale
     float fscale, finv, Tshift, pad1;
+    // bulk tensor copy map of the populations (staged kernel), or null; last,
+    // so that adding it moved no field the other kernels read
+    const void* tmap;
 };
 static_assert(sizeof(InstDesc) % 8 == 0, "descriptor must be 8-byte sized");
 
