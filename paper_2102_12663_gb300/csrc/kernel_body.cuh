@@ -21,6 +21,8 @@
 // model bit for bit; the FP32 instantiation may contract.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 // Resident blocks of 256 threads the step kernel is compiled for (register
@@ -95,8 +97,8 @@ __device__ __forceinline__ Rn<R> operator/(Rn<R> a, Rn<R> b) { return Rn<R>(rn_d
 template <class R>
 __device__ __forceinline__ Rn<R> operator-(Rn<R> a) { return Rn<R>(-a.v); }
 
-template <class R>
-__device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPART], double* out) {
+// FP64 partials: a shuffle tree per warp, then one across the warps.
+__device__ __forceinline__ void warp_block_reduce_f64(double* acc, double (*red)[NPART], double* out) {
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -132,6 +134,50 @@ __device__ __forceinline__ void warp_block_reduce(double* acc, double (*red)[NPA
                 if (lane + off < width) v = k < NSUM ? v + o : fmax(v, o);
             }
             if (lane == 0) out[k] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ double amax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float amax(float a, float b) { return fmaxf(a, b); }
+
+// Block reduction of the per-thread partials acc (A: the storage's
+// accumulator type) into out[NPART] (FP64): sums for slots < NSUM, maxima
+// for the rest.  FP64 partials reduce by a shuffle tree per warp and one more
+// across warps.  FP32 partials (the FP32-arithmetic storages) reduce by an
+// FP32 shuffle tree per warp, then one thread per slot folds the warps'
+// values in FP64 in warp order: GB300's FP64 pipe is narrow, and FP64
+// shuffle trees over every tile made the observing step FP64-bound.
+template <class A>
+__device__ __forceinline__ void warp_block_reduce(A* acc, double (*red)[NPART], double* out) {
+    if constexpr (std::is_same<A, double>::value) {
+        warp_block_reduce_f64(acc, red, out);
+    } else {
+        const int nthreads = blockDim.x * blockDim.y;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int nwarps = (nthreads + 31) >> 5;
+        const int width = min(32, nthreads - (warp << 5));
+        const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) {
+            A v = acc[k];
+            if (__any_sync(mask, v != A(0))) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const A o = __shfl_down_sync(mask, v, off);
+                    if (lane + off < width) v = k < NSUM ? v + o : amax(v, o);
+                }
+            } else {
+                v = A(0);
+            }
+            if (lane == 0) red[warp][k] = (double)v;
+        }
+        __syncthreads();
+        if (tid < NPART) {
+            double v = red[0][tid];
+            for (int w = 1; w < nwarps; ++w) v = tid < NSUM ? v + red[w][tid] : fmax(v, red[w][tid]);
+            out[tid] = v;
         }
     }
 }
@@ -222,10 +268,10 @@ __device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, type
 // The arithmetic runs in Rn<R> (each operation rounded on its own), so the
 // update is the same function of the loaded populations in every kernel that
 // inlines it.
-template <class ST, bool OBS, int PAR>
+template <class ST, bool OBS, int PAR, class A = double>
 __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                                           const typename ST::R* fin, const typename ST::R* gin,
-                                          uint8_t m, int mode, double* acc) {
+                                          uint8_t m, int mode, A* acc) {
     using T = typename ST::T;
     using R = typename ST::R;
     using E = Rn<R>;
@@ -298,13 +344,13 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     // ---- observables of the pre-collision state -----------------------------
     if (OBS) {
         if (mode & OBS_STATS) {
-            acc[P_MASS] += (double)sum18.v;
+            acc[P_MASS] += (A)sum18.v;
             // max of |u|^2; the fold takes one square root (sqrt is monotone)
-            acc[P_PEAK] = fmax(acc[P_PEAK], (double)usq.v);
+            acc[P_PEAK] = amax(acc[P_PEAK], (A)usq.v);
             if (type == FLUID) {
-                acc[P_SUM_P] += (double)p.v;
-                acc[P_N_FLUID] += 1.0;
-                if (!isfinite((double)p.v)) acc[P_NAN] += 1.0;
+                acc[P_SUM_P] += (A)p.v;
+                acc[P_N_FLUID] += A(1);
+                if (!isfinite((double)p.v)) acc[P_NAN] += A(1);
                 if (bnd) {
                     bool hit_c = false, hit_h = false;
                     double ac_x = 0.0, ac_y = 0.0, ah_x = 0.0, ah_y = 0.0;
@@ -330,16 +376,16 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                             if (d.eye_normals) { ax = x - d.arc_xc; ay = y - d.arc_yc; }
                             const double r = sqrt(ax * ax + ay * ay);
                             const double nxw = r > 0.0 ? ax / r : 0.0, nyw = r > 0.0 ? ay / r : 0.0;
-                            acc[P_WSS_C] += fabs(-nyw * (sxx * nxw + sxy * nyw) + nxw * (sxy * nxw + syy * nyw));
-                            acc[P_N_C] += 1.0;
+                            acc[P_WSS_C] += (A)fabs(-nyw * (sxx * nxw + sxy * nyw) + nxw * (sxy * nxw + syy * nyw));
+                            acc[P_N_C] += A(1);
                         }
                         if (hit_h) {
                             double ax = ah_x, ay = ah_y;
                             if (d.eye_normals) { ax = 0.0; ay = 1.0; }
                             const double r = sqrt(ax * ax + ay * ay);
                             const double nxw = r > 0.0 ? ax / r : 0.0, nyw = r > 0.0 ? ay / r : 0.0;
-                            acc[P_WSS_I] += fabs(-nyw * (sxx * nxw + sxy * nyw) + nxw * (sxy * nxw + syy * nyw));
-                            acc[P_N_I] += 1.0;
+                            acc[P_WSS_I] += (A)fabs(-nyw * (sxx * nxw + sxy * nyw) + nxw * (sxy * nxw + syy * nyw));
+                            acc[P_N_I] += A(1);
                         }
                     }
                 }
@@ -350,7 +396,7 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
             if ((mode & OBS_RESID) && d.snap_valid) {
                 const double dx = (double)ux.v - (double)U[c];
                 const double dy = (double)uy.v - (double)U[np + c];
-                acc[P_RESID] = fmax(acc[P_RESID], dx * dx + dy * dy);
+                acc[P_RESID] = amax(acc[P_RESID], (A)(dx * dx + dy * dy));
             }
             if (mode & OBS_SNAP) {
                 U[c] = ux.v;
@@ -480,20 +526,20 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         }
     }
     if (OBS && (mode & OBS_STATS)) {
-        acc[P_Q_IN] += q_in;
-        acc[P_Q_OUT] += q_out;
+        acc[P_Q_IN] += (A)q_in;
+        acc[P_Q_OUT] += (A)q_out;
     }
 }
 
-template <class ST, bool OBS, int PAR>
-__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode, double* acc) {
+template <class ST, bool OBS, int PAR, class A = double>
+__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode, A* acc) {
     using R = typename ST::R;
     int nb[9];
     neighbours(d, x, y, nb);
     R f[9], g[4];
     uint8_t m;
     load_cell<ST, PAR>(d, nb, f, g, m);
-    cell_body<ST, OBS, PAR>(d, x, y, f, g, m, mode, acc);
+    cell_body<ST, OBS, PAR, A>(d, x, y, f, g, m, mode, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -636,12 +682,12 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
 // velocity snapshot.  Interior cells have no wall, inlet or outlet link, so
 // they add nothing to the wall shear stress or the fluxes.  Same definitions
 // as cell_body (Eq. 9), evaluated in the pair path's FP32 arithmetic.  The
-// two cells are combined in FP32 first (a sum of two values, a maximum, a
-// count) and enter the FP64 partials once per pair: GB300's FP64 pipe is
-// narrow, and per-cell FP64 updates made this step FP64-bound.
-template <class ST>
+// two cells are combined first (a sum of two values, a maximum, a count) and
+// enter the partials (type A) once per pair: GB300's FP64 pipe is narrow, and
+// per-cell FP64 updates made this step FP64-bound.
+template <class ST, class A>
 __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, const float* a,
-                                             const float* b, uint32_t m2, int mode, double* acc) {
+                                             const float* b, uint32_t m2, int mode, A* acc) {
     const int np = (int)d.npad;
     const int c = y * d.nx + x;
     float ux2[2], uy2[2], mass = 0.0f, psum = 0.0f, pk = 0.0f;
@@ -667,11 +713,11 @@ __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, co
         }
     }
     if (mode & OBS_STATS) {
-        acc[P_MASS] += (double)mass;
-        acc[P_PEAK] = fmax(acc[P_PEAK], (double)pk);
-        acc[P_SUM_P] += (double)psum;
-        acc[P_N_FLUID] += (double)nfl;
-        if (bad) acc[P_NAN] += 1.0;
+        acc[P_MASS] += (A)mass;
+        acc[P_PEAK] = amax(acc[P_PEAK], (A)pk);
+        acc[P_SUM_P] += (A)psum;
+        acc[P_N_FLUID] += (A)nfl;
+        if (bad) acc[P_NAN] += A(1);
     }
     if (mode & (OBS_RESID | OBS_SNAP)) {
         float* U = static_cast<float*>(d.usnap);
@@ -683,7 +729,7 @@ __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, co
                 const float dy = uy2[j] - U[np + c + j];
                 r2 = fmaxf(r2, dx * dx + dy * dy);
             }
-            acc[P_RESID] = fmax(acc[P_RESID], (double)r2);
+            acc[P_RESID] = amax(acc[P_RESID], (A)r2);
         }
         if (mode & OBS_SNAP) {
 #pragma unroll
@@ -695,10 +741,10 @@ __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, co
     }
 }
 
-template <class ST, int PAR, bool OBS = false>
+template <class ST, int PAR, bool OBS = false, class A = double>
 __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, int y, bool por0,
                                                      bool por1, uint32_t m2 = 0, int mode = 0,
-                                                     double* acc = nullptr) {
+                                                     A* acc = nullptr) {
     using T = typename ST::T;
     const int nx = d.nx, ny = d.ny;
     const int np = (int)d.npad;
@@ -756,13 +802,13 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
         }
     }
 
-    if constexpr (OBS) pair_observe<ST>(d, x, y, a, b, m2, mode, acc);
+    if constexpr (OBS) pair_observe<ST, A>(d, x, y, a, b, m2, mode, acc);
     pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
 }
 
-template <class ST, bool OBS, int PAR>
+template <class ST, bool OBS, int PAR, class A = double>
 __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, int rpt,
-                                          double* acc) {
+                                          A* acc) {
     constexpr int V = sizeof(typename ST::R) == 4 ? 2 : 1;
     const int x = te.z + V * threadIdx.x;
     if constexpr (V == 2) {
@@ -788,19 +834,19 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
                     fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
                 }
                 if (fast)
-                    update_pair_interior<ST, PAR, OBS>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
+                    update_pair_interior<ST, PAR, OBS, A>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
                                                        (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode,
                                                        acc);
             }
             if (!fast) {
-                if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);
-                if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x + 1, y, mode, acc);
+                if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
+                if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x + 1, y, mode, acc);
             }
         }
     } else {
         for (int r = 0; r < rpt; ++r) {
             const int y = te.w + threadIdx.y + r * blockDim.y;
-            if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR>(sd, x, y, mode, acc);
+            if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
         }
     }
 }
@@ -1000,8 +1046,8 @@ __device__ __forceinline__ void ws_segment(const InstDesc& d, const typename ST:
     const int c = 2 * lane;  // column of cell x in the segment
     const int x = m.x + c, y = m.y;
     if (m.flags & WS_DIRECT) {
-        if (x < nx) update_cell<ST, false, PAR>(d, x, y, 0, nullptr);
-        if (x + 1 < nx) update_cell<ST, false, PAR>(d, x + 1, y, 0, nullptr);
+        if (x < nx) update_cell<ST, false, PAR, double>(d, x, y, 0, nullptr);
+        if (x + 1 < nx) update_cell<ST, false, PAR, double>(d, x + 1, y, 0, nullptr);
         return;
     }
     // a staged instance has nx a multiple of the 16-byte chunk, hence even:
@@ -1026,8 +1072,8 @@ __device__ __forceinline__ void ws_segment(const InstDesc& d, const typename ST:
     if (!in) return;
     if ((m2 & TYPE_BITS) > POROUS && ((m2 >> 8) & TYPE_BITS) > POROUS) return;  // neither cell active
     if (edge) {
-        update_cell<ST, false, PAR>(d, x, y, 0, nullptr);
-        update_cell<ST, false, PAR>(d, x + 1, y, 0, nullptr);
+        update_cell<ST, false, PAR, double>(d, x, y, 0, nullptr);
+        update_cell<ST, false, PAR, double>(d, x + 1, y, 0, nullptr);
         return;
     }
     ws_load<ST, PAR>(d, stage, c, a, b);
@@ -1046,7 +1092,7 @@ __device__ __forceinline__ void ws_segment(const InstDesc& d, const typename ST:
         for (int i = 0; i < 9; ++i) f[i] = c[i];
 #pragma unroll
         for (int i = 0; i < 4; ++i) g[i] = c[9 + i];
-        cell_body<ST, false, PAR>(d, x + v, y, f, g, (uint8_t)(m2 >> (8 * v)), 0, nullptr);
+        cell_body<ST, false, PAR, double>(d, x + v, y, f, g, (uint8_t)(m2 >> (8 * v)), 0, nullptr);
     }
 }
 
@@ -1234,7 +1280,11 @@ __global__ void __launch_bounds__(WS_THREADS, LBM_WS_MINB) step_kernel_ws(const 
     }
 }
 
-template <class ST, bool OBS>
+// One time step of a tile list.  OBS adds the observables of the
+// pre-collision state, with per-thread and per-warp partials of type A: FP64
+// for observe-only reads, the storage's accumulator type for the steady-state
+// check step (which also writes).
+template <class ST, bool OBS, class A = double>
 __global__ void __launch_bounds__(256, OBS ? 2 : step_min_blocks<ST>()) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
@@ -1258,13 +1308,13 @@ __global__ void __launch_bounds__(256, OBS ? 2 : step_min_blocks<ST>()) step_ker
         // completed and its writes are visible before any population is touched
         grid_dependency_wait();
         const int parity = (sd.parity ^ flip) & 1;
-        double acc[NPART];
+        A acc[NPART];
 #pragma unroll
-        for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
-        if (parity) tile_rows<ST, OBS, 1>(sd, te, mode, shape.rpt, acc);
-        else tile_rows<ST, OBS, 0>(sd, te, mode, shape.rpt, acc);
+        for (int k = 0; k < NPART; ++k) acc[k] = A(0);
+        if (parity) tile_rows<ST, OBS, 1, A>(sd, te, mode, shape.rpt, acc);
+        else tile_rows<ST, OBS, 0, A>(sd, te, mode, shape.rpt, acc);
         if (OBS && (mode & OBS_STATS)) {
-            warp_block_reduce<double>(acc, red, sd.partials + (int64_t)(te.y & TILE_INDEX) * NPART);
+            warp_block_reduce<A>(acc, red, sd.partials + (int64_t)(te.y & TILE_INDEX) * NPART);
         }
     }
 }

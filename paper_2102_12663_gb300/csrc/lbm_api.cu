@@ -23,14 +23,14 @@ bool build_mask(const lbm_geometry_desc& g, uint8_t* out, lbm_geometry_info* inf
                 std::string& err);
 void mark_near_boundary(uint8_t* m, int nx, int ny);
 
-StepPlan step_plan(int precision, bool obs, Shape shape) {
-    return precision == 0 ? step_plan_f64(obs, shape) : step_plan_lp(precision, obs, shape);
+StepPlan step_plan(int precision, int mode, Shape shape) {
+    return precision == 0 ? step_plan_f64(mode, shape) : step_plan_lp(precision, mode, shape);
 }
 
 cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
                         int flip, int mode, Shape shape, int grid, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    const StepPlan pl = step_plan(precision, mode != 0, shape);
+    const StepPlan pl = step_plan(precision, mode, shape);
     if (pl.max_grid > 0) grid = std::min(grid, pl.max_grid);
     void* args[] = {&insts, &tiles, &ntiles, &flip, &mode, &shape};
     return cudaLaunchKernel(pl.func, dim3(grid), pl.block, args, pl.smem, s);
@@ -909,7 +909,7 @@ static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int
         cudaStreamDestroy(cs);
         return e;
     }
-    const StepPlan pl = step_plan(prec, false, sh);
+    const StepPlan pl = step_plan(prec, 0, sh);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         const InstDesc* a0 = insts;
         const int4* a1 = tiles;

@@ -133,6 +133,7 @@ template <int POL = ST_STREAM>
 struct StF64T {
     using T = double;
     using R = double;
+    using A = double;  // per-thread and per-warp partials of the observables
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
@@ -145,6 +146,7 @@ template <int POL = ST_STREAM>
 struct StF32T {
     using T = float;
     using R = float;
+    using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
@@ -166,6 +168,7 @@ template <int POL = ST_STREAM>
 struct StF16T {
     using T = __half;
     using R = float;
+    using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __half2float(__ldcg(p)) * d.finv;
     }
@@ -202,6 +205,7 @@ template <int POL = ST_STREAM>
 struct StBF16T {
     using T = __nv_bfloat16;
     using R = float;
+    using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __bfloat162float(__ldcg(p)) * d.finv;
     }
@@ -256,12 +260,13 @@ struct StepPlan {
     size_t smem;
     int max_grid = 0;  // persistent kernels: co-resident blocks on the device (0: no cap)
 };
-StepPlan step_plan(int precision, bool obs, Shape shape);
+// mode: the step's observation mode (0 for a plain step)
+StepPlan step_plan(int precision, int mode, Shape shape);
 // status word of the staged kernel: 0, or 1 after one of its waits expired
 // (read and cleared)
 cudaError_t take_step_status(int* status);
-StepPlan step_plan_f64(bool obs, Shape shape);
-StepPlan step_plan_lp(int precision, bool obs, Shape shape);
+StepPlan step_plan_f64(int mode, Shape shape);
+StepPlan step_plan_lp(int precision, int mode, Shape shape);
 // Dataflow kernel advancing a tile list by many steps in one cooperative
 // launch; keep = L2-resident stores (sweeps of several steps).
 StepPlan flow_plan(int precision, Shape shape, bool keep);

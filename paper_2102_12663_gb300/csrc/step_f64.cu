@@ -5,9 +5,9 @@
 
 namespace lbm {
 
-StepPlan step_plan_f64(bool obs, Shape shape) {
+StepPlan step_plan_f64(int mode, Shape shape) {
     StepPlan p;
-    p.func = obs ? reinterpret_cast<const void*>(&step_kernel<StF64, true>)
+    p.func = mode != 0 ? reinterpret_cast<const void*>(&step_kernel<StF64, true>)
                  : reinterpret_cast<const void*>(&step_kernel<StF64, false>);
     p.block = dim3(shape.tw, shape.bh);
     p.smem = 0;

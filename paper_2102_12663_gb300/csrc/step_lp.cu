@@ -10,7 +10,8 @@
 namespace lbm {
 
 template <class ST>
-static StepPlan plan_t(bool obs, Shape shape) {
+static StepPlan plan_t(int mode, Shape shape) {
+    const bool obs = mode != 0;
     StepPlan p;
     if (!obs && shape.bh == 1 && shape.tw >= WS_SEG) {
         const void* f = reinterpret_cast<const void*>(&step_kernel_ws<ST>);
@@ -33,19 +34,22 @@ static StepPlan plan_t(bool obs, Shape shape) {
         }
         p.max_grid = cap[dev] > 0 ? cap[dev] : 1;
     } else {
-        p.func = obs ? reinterpret_cast<const void*>(&step_kernel<ST, true>)
-                     : reinterpret_cast<const void*>(&step_kernel<ST, false>);
+        // the steady-state check step (observe and write) folds its partials
+        // in FP32 per warp; observe-only reads keep FP64 partials
+        p.func = !obs ? reinterpret_cast<const void*>(&step_kernel<ST, false>)
+                 : (mode & OBS_WRITE) ? reinterpret_cast<const void*>(&step_kernel<ST, true, typename ST::A>)
+                                      : reinterpret_cast<const void*>(&step_kernel<ST, true>);
         p.block = dim3(shape.tw / cells_per_thread(1), shape.bh);
         p.smem = 0;
     }
     return p;
 }
 
-StepPlan step_plan_lp(int precision, bool obs, Shape shape) {
+StepPlan step_plan_lp(int precision, int mode, Shape shape) {
     switch (precision) {
-    case 1: return plan_t<StF32>(obs, shape);
-    case 2: return plan_t<StF16>(obs, shape);
-    default: return plan_t<StBF16>(obs, shape);
+    case 1: return plan_t<StF32>(mode, shape);
+    case 2: return plan_t<StF16>(mode, shape);
+    default: return plan_t<StBF16>(mode, shape);
     }
 }
 
