@@ -273,7 +273,9 @@ def run_gpu(args):
         clk = clocks.stop()
 
         # end to end through the public API: parameters in (host -> device
-        # descriptor upload) and observables out (device -> host) every step
+        # descriptor upload) and the step's result out every step: the check's
+        # observables, read back by the steady-state loop (device -> host) and
+        # returned by last_observables
         h2d = 0
         d2h = 0
         torch.cuda.synchronize()
@@ -281,11 +283,11 @@ def run_gpu(args):
         for _ in range(args.steps):
             dom.set_params(pp)
             bench_step()
-            dom.observables()
+            dom.last_observables()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        h2d = 312  # descriptor bytes uploaded by set_params
-        d2h = 2 * 12 * 8  # residual check + observables read-back
+        h2d = 368  # the instance descriptor uploaded by set_params
+        d2h = 12 * 8 + 4  # the check's observables and the dataflow status word
 
     t_max = total_ms
     if world > 1:

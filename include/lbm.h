@@ -272,7 +272,8 @@ lbm_status lbm_step(lbm_domain* dom, int64_t nsteps);
  * speed needs each check before the next interval), so the loop may stop one
  * interval after the check that met the criterion; *steps_out includes it.
  * Returns with the stream synchronised.  Allocates a small pinned host
- * buffer on first use. */
+ * buffer on first use.  The last check's observables are then available from
+ * lbm_last_observables. */
 lbm_status lbm_run_to_steady(lbm_domain* dom, double tol, int32_t check_every,
                              int64_t max_steps, int64_t* steps_out);
 
@@ -401,7 +402,12 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
  * are then available from lbm_last_observables. */
 lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every);
 
-/* Observables of the domain's last batch check (EINVAL if none). */
+/* Observables of the domain's last steady-state check: the last check
+ * interval that lbm_run_to_steady processed (including an interval queued
+ * ahead that ran after the converging check) or the last lbm_batch_check.
+ * `step` is the step count of the observed state; the sums are the check
+ * step's (FP32 partials per warp for the FP32-arithmetic storages, folded in
+ * FP64).  A host copy: no device work.  EINVAL if no check has run. */
 lbm_status lbm_last_observables(const lbm_domain* dom, lbm_observables* out);
 
 /* Launch shape of the batch (switches every member). */

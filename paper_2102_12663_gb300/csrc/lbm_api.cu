@@ -179,7 +179,7 @@ struct lbm_domain {
     int64_t n_curved = 0;             // cells with a curved-cornea link
     lbm_batch* batch = nullptr;       // batch this domain belongs to, if any
     cudaStream_t own_stream = nullptr;
-    lbm_observables last_obs{};       // observables of the last batch check
+    lbm_observables last_obs{};       // observables of the last steady-state check
     bool have_last_obs = false;
 };
 
@@ -1109,6 +1109,7 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
     // before the host reads a check, and the loop may stop one interval after
     // the check that met the criterion (*steps_out counts it).
     const bool ahead = d->h.tm_model != 1;
+    const int64_t s0 = d->step;  // interval k observes the state after s0 + k check_every - 1 steps
     int64_t taken = 0, queued = 0;
     int slot = 0;
     lbm_status st = LBM_OK;
@@ -1146,6 +1147,8 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
                 drain();
                 return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
             }
+            fill_obs(d, o, s0 + taken - 1, &d->last_obs);
+            d->have_last_obs = true;
             update_seepage(d, o[O_IOP]);
             if (d->h.tm_model == 1) {
                 if ((st = upload_desc(d)) != LBM_OK) return st;
@@ -1160,6 +1163,7 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
                     }
                     if (t[O_NAN] != 0.0)
                         return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)queued);
+                    fill_obs(d, t, s0 + queued - 1, &d->last_obs);
                     update_seepage(d, t[O_IOP]);
                 }
                 return LBM_OK;
@@ -1630,7 +1634,7 @@ extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
 
 extern "C" lbm_status lbm_last_observables(const lbm_domain* d, lbm_observables* out) {
     if (!d || !out) return fail(LBM_EINVAL, "null argument");
-    if (!d->have_last_obs) return fail(LBM_EINVAL, "no batch check has observed this domain yet");
+    if (!d->have_last_obs) return fail(LBM_EINVAL, "no steady-state check has observed this domain yet");
     *out = d->last_obs;
     return LBM_OK;
 }

@@ -335,7 +335,8 @@ class Domain:
         return {k: getattr(o, k) for k, _ in Observables._fields_}
 
     def last_observables(self) -> dict:
-        """Observables of the last batch check of this domain."""
+        """Observables of the last steady-state check of this domain
+        (run_to_steady or a batch check): a host copy, no device work."""
         o = Observables()
         check(self._L.lbm_last_observables(self._h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in Observables._fields_}

@@ -374,6 +374,30 @@ def test_staged_kernel_eye(prec, nx, ny, launch):
         assert rel_err(dom, ref) <= bound, done
 
 
+@pytest.mark.parametrize("stepping", [lbm.STEP_FLOW, lbm.STEP_PER_LAUNCH])
+def test_last_observables_after_steady_loop(stepping):
+    """lbm_last_observables after lbm_run_to_steady returns the last check's
+    observables: those of the state after 99 steps (the check observes before
+    its own update), as a separate domain stepped 99 times reads them, to the
+    FP32 partials' precision; the residual of the second check is defined."""
+    launch = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=stepping)
+    dom, _, pp = eye_pair(160, 80, "f32", launch=launch)
+    with pytest.raises(lbm.LBMError):
+        dom.last_observables()
+    st, steps = dom.run_to_steady(0.0, check_every=50, max_steps=100)
+    assert steps == 100 and dom.step_count == 100
+    got = dom.last_observables()
+    twin, _, _ = eye_pair(160, 80, "f32", launch=launch)
+    twin.step(99)
+    ref = twin.observables()
+    assert got["step"] == 99 and ref["step"] == 99
+    for k in ("iop", "mass", "peak_speed", "wss_cornea", "wss_iris", "q_in", "q_out"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-5), k
+    for k in ("n_fluid", "n_cornea", "n_iris", "nan_flag"):
+        assert got[k] == ref[k], k
+    assert got["residual"] > 0.0
+
+
 def test_supine_eye_mirror_symmetry_fp32():
     """The supine eye without noise stays mirror-symmetric on the FP32 path
     (cell pairs, shuffled x-shifted links in both directions)."""
