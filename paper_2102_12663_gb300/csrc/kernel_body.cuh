@@ -25,11 +25,17 @@
 
 #include "lbm_internal.cuh"
 
-// Resident blocks of 256 threads the step kernel is compiled for (register
+// Resident blocks of 256 threads the kernels are compiled for (register
 // budget 65536 / (256 * n)): the two-cell pair path keeps 26 populations and
-// the collision temporaries of two cells live.
+// the collision temporaries of two cells live.  FP32 storage, one launch per
+// step: 4 (64 registers, a few spilled bytes; more warps to hide memory
+// latency measured faster than 3).  FP32 dataflow kernel: 3 (its per-tile
+// waits and barriers do better with fewer, fatter blocks).  FP64: 3.
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 3
+#define LBM_STEP_MIN_BLOCKS 4
+#endif
+#ifndef LBM_FLOW_MIN_BLOCKS
+#define LBM_FLOW_MIN_BLOCKS 3
 #endif
 // the same for the 16-bit storages (which convert on every load and store)
 #ifndef LBM_STEP_MIN_BLOCKS_16
@@ -40,7 +46,12 @@ namespace lbm {
 
 template <class ST>
 constexpr int step_min_blocks() {
-    return sizeof(typename ST::T) == 2 ? LBM_STEP_MIN_BLOCKS_16 : LBM_STEP_MIN_BLOCKS;
+    return sizeof(typename ST::T) == 2 ? LBM_STEP_MIN_BLOCKS_16
+                                       : (sizeof(typename ST::T) == 4 ? LBM_STEP_MIN_BLOCKS : 3);
+}
+template <class ST>
+constexpr int flow_min_blocks() {
+    return sizeof(typename ST::T) == 2 ? LBM_STEP_MIN_BLOCKS_16 : (sizeof(typename ST::T) == 4 ? LBM_FLOW_MIN_BLOCKS : 3);
 }
 
 // Free constants of Eq. 7 (lambda + gamma = sigma, lambda + 2 gamma = 1/2)
@@ -1377,7 +1388,7 @@ __device__ __forceinline__ void flow_wait(const int* done, int target, int* flag
 }
 
 template <class ST>
-__global__ void __launch_bounds__(256, step_min_blocks<ST>())
+__global__ void __launch_bounds__(256, flow_min_blocks<ST>())
     step_kernel_flow(const InstDesc* __restrict__ insts, const FlowArgs fa, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
