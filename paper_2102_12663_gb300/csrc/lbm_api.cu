@@ -207,11 +207,17 @@ static int grid_of(const lbm_domain* d, int ntiles) {
     return std::max(1, std::min(ntiles, d->launch.blocks_per_sm * d->num_sms));
 }
 
-// Launch order of the per-step kernels: tiles with boundary cells (slower:
-// the general per-cell update) first, pure tiles after, each in list order.
-// Each entry carries its own tile index, so the order changes nothing but
-// which blocks run last: fast tiles, which shortens a step's tail.
+// Launch order of a domain's per-step kernels.  On a large tile list (many
+// waves of blocks per step) tiles with boundary cells (slower: the general
+// per-cell update) go first and pure tiles after, each in list order, so the
+// last blocks of a step run fast tiles and the step's tail shortens.  Each
+// entry carries its own tile index, so the order changes nothing else.  On
+// small grids and merged batch lists the raster order measured faster, so
+// they keep it.
+static constexpr size_t BOUNDARY_FIRST_MIN_TILES = 4096;
+
 static std::vector<int4> boundary_tiles_first(const std::vector<int4>& tiles) {
+    if (tiles.size() < BOUNDARY_FIRST_MIN_TILES) return tiles;
     std::vector<int4> order;
     order.reserve(tiles.size());
     for (const int4& t : tiles)
@@ -1519,10 +1525,9 @@ static lbm_status batch_rebuild(lbm_batch* b) {
         }
     }
     if ((int64_t)tiles.size() > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded");
-    const std::vector<int4> launch_order = boundary_tiles_first(tiles);
     if (!tiles.empty()) {
-        CK(cudaMemcpyAsync(b->d_tiles, launch_order.data(), launch_order.size() * sizeof(int4),
-                           cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                           b->stream));
         CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, b->stream));
         CK(cudaMemcpyAsync(b->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice,
