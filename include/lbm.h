@@ -209,7 +209,9 @@ typedef struct lbm_observables {
  *     and tile_w >= 64 take a persistent kernel (grid capped at the blocks
  *     the device holds at once) whose warps stage population rows in shared
  *     memory by bulk tensor copies; its interior collision rounds differently
- *     in the last bit.
+ *     in the last bit.  A domain of at least 4096 tiles launches the tiles
+ *     that hold boundary cells first (the slower ones), which shortens the
+ *     tail of each step; the results do not depend on the order.
  * The dataflow kernel (any sweep) and the per-step direct kernel give
  * bit-identical populations.  Observing steps and batches always take one
  * launch per step. */
