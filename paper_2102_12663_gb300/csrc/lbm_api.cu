@@ -96,7 +96,7 @@ static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct Layout {
     int64_t npad, max_tiles;
-    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, total;
+    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, fold, total;
     int64_t max_curved;
 };
 
@@ -133,6 +133,7 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.usnap = off; off = align_up(off + 2 * (size_t)L.npad * real_size(prec));
     L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
     L.tmap = off; off = align_up(off + sizeof(CUtensorMap));
+    L.fold = off; off = align_up(off + ((size_t)FOLD_MAX * NPART + 1) * sizeof(double));
     L.total = off;
     return true;
 }
@@ -542,16 +543,42 @@ __global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, doubl
     }
 }
 
-// Folds the per-tile partials of each instance in a fixed order (one block per
-// instance, thread-strided then a fixed binary tree), so the result does not
-// depend on how tiles were scheduled or on which other instances ran.
-__global__ void __launch_bounds__(256) finalize_kernel(const InstDesc* __restrict__ insts) {
-    const InstDesc& d = insts[blockIdx.x];
+// Observables of an instance from its folded partials a[NPART].
+__device__ void write_obs(const InstDesc& d, const double* a) {
+    double* o = d.obs;
+    o[O_IOP] = a[P_N_FLUID] > 0.0 ? a[P_SUM_P] / a[P_N_FLUID] : 0.0;
+    o[O_Q_IN] = a[P_Q_IN];
+    o[O_Q_OUT] = a[P_Q_OUT];
+    o[O_MASS] = a[P_MASS];
+    o[O_PEAK] = sqrt(a[P_PEAK]);  // the partials hold max |u|^2
+    o[O_WSS_C] = a[P_N_C] > 0.0 ? a[P_WSS_C] / a[P_N_C] : 0.0;
+    o[O_WSS_I] = a[P_N_I] > 0.0 ? a[P_WSS_I] / a[P_N_I] : 0.0;
+    o[O_RESID] = d.snap_valid ? sqrt(a[P_RESID]) : -1.0;
+    o[O_N_FLUID] = a[P_N_FLUID];
+    o[O_N_C] = a[P_N_C];
+    o[O_N_I] = a[P_N_I];
+    o[O_NAN] = (a[P_NAN] > 0.0 || !isfinite(a[P_SUM_P]) || !isfinite(a[P_MASS])) ? 1.0 : 0.0;
+}
+
+// Folds the per-tile partials of each instance in a fixed order, so the
+// result does not depend on how tiles were scheduled or on which other
+// instances ran.  fb blocks share an instance: block b folds the b-th of fb
+// contiguous tile ranges (thread-strided, then a fixed binary tree) and
+// stores its partial; the block that arrives last folds the fb partials in
+// block order and writes the observables.  GB300's FP64 pipe is narrow, so
+// one block per instance made this fold the long pole of a check interval
+// on large grids.
+__global__ void __launch_bounds__(256) finalize_kernel(const InstDesc* __restrict__ insts, int fb) {
+    const int inst = blockIdx.x / fb, b = blockIdx.x - inst * fb;
+    const InstDesc& d = insts[inst];
     __shared__ double sm[256][NPART];
+    __shared__ int last;
     double acc[NPART];
     for (int k = 0; k < NPART; ++k) acc[k] = 0.0;
     const int nt = d.ntiles;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int chunk = (nt + fb - 1) / fb;
+    const int t1 = min(nt, (b + 1) * chunk);
+    for (int t = b * chunk + (int)threadIdx.x; t < t1; t += blockDim.x) {
         const double* q = d.partials + (int64_t)t * NPART;
         for (int k = 0; k < NSUM; ++k) acc[k] += q[k];
         for (int k = NSUM; k < NPART; ++k) acc[k] = fmax(acc[k], q[k]);
@@ -566,28 +593,42 @@ __global__ void __launch_bounds__(256) finalize_kernel(const InstDesc* __restric
         }
         __syncthreads();
     }
+    if (fb == 1) {
+        if (threadIdx.x == 0) write_obs(d, sm[0]);
+        return;
+    }
+    double* const part = d.fold;
+    unsigned int* const arrived = reinterpret_cast<unsigned int*>(d.fold + FOLD_MAX * NPART);
+    if (threadIdx.x < NPART) part[b * NPART + threadIdx.x] = sm[0][threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(arrived, 1u) == (unsigned int)(fb - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < NPART) {
+        const int k = threadIdx.x;
+        double v = __ldcg(part + k);
+        for (int bb = 1; bb < fb; ++bb) {
+            const double w = __ldcg(part + bb * NPART + k);
+            v = k < NSUM ? v + w : fmax(v, w);
+        }
+        sm[0][k] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double* a = sm[0];
-        double* o = d.obs;
-        o[O_IOP] = a[P_N_FLUID] > 0.0 ? a[P_SUM_P] / a[P_N_FLUID] : 0.0;
-        o[O_Q_IN] = a[P_Q_IN];
-        o[O_Q_OUT] = a[P_Q_OUT];
-        o[O_MASS] = a[P_MASS];
-        o[O_PEAK] = sqrt(a[P_PEAK]);  // the partials hold max |u|^2
-        o[O_WSS_C] = a[P_N_C] > 0.0 ? a[P_WSS_C] / a[P_N_C] : 0.0;
-        o[O_WSS_I] = a[P_N_I] > 0.0 ? a[P_WSS_I] / a[P_N_I] : 0.0;
-        o[O_RESID] = d.snap_valid ? sqrt(a[P_RESID]) : -1.0;
-        o[O_N_FLUID] = a[P_N_FLUID];
-        o[O_N_C] = a[P_N_C];
-        o[O_N_I] = a[P_N_I];
-        o[O_NAN] = (a[P_NAN] > 0.0 || !isfinite(a[P_SUM_P]) || !isfinite(a[P_MASS])) ? 1.0 : 0.0;
+        write_obs(d, sm[0]);
+        *arrived = 0u;  // ready for the next fold
     }
 }
 
 namespace lbm {
 cudaError_t launch_finalize(const InstDesc* insts, int ninst, cudaStream_t s) {
     if (ninst <= 0) return cudaSuccess;
-    finalize_kernel<<<ninst, 256, 0, s>>>(insts);
+    // a few dozen blocks in all: one instance spreads over FOLD_MAX blocks,
+    // a batch of 64 or more takes one block each
+    const int fb = std::max(1, std::min(FOLD_MAX, 64 / ninst));
+    finalize_kernel<<<ninst * fb, 256, 0, s>>>(insts, fb);
     return cudaGetLastError();
 }
 }  // namespace lbm
@@ -742,6 +783,7 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
         delete d;
         return st;
     }
+    h.fold = reinterpret_cast<double*>(d->base + d->L.fold);
     h.qcol = reinterpret_cast<const int32_t*>(d->base + d->L.qcol);
     h.qtab = reinterpret_cast<const CurvedCell*>(d->base + d->L.qtab);
     cudaError_t ce = cudaMemcpyAsync(d->base + d->L.mask, d->hmask.data(), (size_t)d->N,
@@ -759,6 +801,11 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
             return fail(LBM_ECUDA, "tensor map upload failed: %s", cudaGetErrorString(ce));
         }
         h.tmap = d->base + d->L.tmap;
+    }
+    ce = cudaMemsetAsync(d->base + d->L.fold, 0, ((size_t)FOLD_MAX * NPART + 1) * sizeof(double), d->stream);
+    if (ce != cudaSuccess) {
+        delete d;
+        return fail(LBM_ECUDA, "fold counter reset failed: %s", cudaGetErrorString(ce));
     }
     ce = cudaMemsetAsync(d->d_flags, 0, sizeof(int), d->stream);
     if (ce != cudaSuccess) {

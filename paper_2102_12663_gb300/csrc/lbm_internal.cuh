@@ -90,7 +90,12 @@ struct InstDesc {
     // bulk tensor copy map of the populations (staged kernel), or null; last,
     // so that adding it moved no field the other kernels read
     const void* tmap;
+    // FOLD_MAX x NPART doubles of per-block partials for the observables'
+    // fold, then its arrival counter (zero between folds)
+    double* fold;
 };
+// most blocks that fold one instance's tile partials
+constexpr int FOLD_MAX = 32;
 static_assert(sizeof(InstDesc) % 8 == 0, "descriptor must be 8-byte sized");
 
 template <class R>
