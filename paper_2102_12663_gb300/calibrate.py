@@ -13,6 +13,37 @@ from __future__ import annotations
 
 from . import lbm
 
+# Porosity labels of the meshwork permeability.  Tab. 5 pairs each
+# permeability K of the TM with a porosity e; the pairs follow the
+# Kozeny-Carman form K = C e^3 / (1 - e)^2 with one constant, C = 4.27e-13 m^2
+# (every row within 0.5 %).  The model's Darcy law (Eq. 4) has no porosity:
+# these functions only translate between the two labels.
+KOZENY_CARMAN_C = 4.27e-13  # m^2
+
+
+def permeability_from_porosity(eps: float, c: float = KOZENY_CARMAN_C) -> float:
+    """K(e) = c e^3 / (1 - e)^2 in m^2, for 0 <= e < 1."""
+    if not 0.0 <= eps < 1.0:
+        raise ValueError("porosity must lie in [0, 1)")
+    return c * eps ** 3 / (1.0 - eps) ** 2
+
+
+def porosity_from_permeability(k: float, c: float = KOZENY_CARMAN_C) -> float:
+    """The porosity e in [0, 1) with K(e) = k (K is increasing in e), by
+    bisection to double precision."""
+    if not k >= 0.0:
+        raise ValueError("permeability must be non-negative")
+    lo, hi = 0.0, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if c * mid ** 3 / (1.0 - mid) ** 2 < k:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
 
 def calibrate_tm_thickness(geometry: dict, params: dict, target_iop_pa: float, h0: float,
                            h1: float, precision: str = "f32", tol_pa: float = 0.5,
