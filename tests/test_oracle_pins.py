@@ -455,3 +455,117 @@ def test_bouzidi_places_the_wall_second_order(q0):
         assert 3.0 < a / b < 5.0
     halfway = _fractional_wall_profile(32, q0, 0)
     assert errs[-1] < halfway / 10
+
+
+def test_residual_of_decaying_shear_waves():
+    """Steady-state residual (max over cells of |u(t) - u(t - D)|): two
+    crossed shear waves u_x = U sin(k y), u_y = V sin(k x) in a periodic box
+    each decay as exp(-nu k^2 t) with nu from Eq. 10, so at the cell where
+    both sines are 1 the residual over an interval of D steps ending at t is
+    sqrt(U^2 + V^2) e^{-nu k^2 (t - D)} (1 - e^{-nu k^2 D}).  Different
+    amplitudes make a dropped component, a squared norm or max |u| fail."""
+    n, tau, U, V = 64, 0.8, 1e-5, 2e-5
+    k = 2 * math.pi / n
+    nu = (2 * tau - 1) / 6
+    m = np.zeros((n, n), np.uint8)
+    s = O.State(O.mask_geom(n, n, 1, 1), O.make_params(tau=tau), m)
+    for y in range(n):
+        for x in range(n):
+            s.f[:, y * n + x] = O.feq(0.0, U * math.sin(k * y), V * math.sin(k * x))
+    assert s.observe()["residual"] == -1.0  # no snapshot yet
+    t0, D = 300, 200
+    s.run(t0)
+    snap = s.fields()[0].copy()
+    assert s.observe(snap)["residual"] == 0.0
+    s.run(D)
+    r = s.observe(snap)["residual"]
+    expect = math.hypot(U, V) * math.exp(-nu * k * k * t0) * (1 - math.exp(-nu * k * k * D))
+    assert r == pytest.approx(expect, rel=2e-2)
+
+
+def test_advected_temperature_wave():
+    """The advective term of Eq. 12, T_i^eq = (T/4)(1 + 2 e_i.u): its first
+    moment is T u, so in a uniform flow u0 a temperature wave translates at
+    u0 and decays at theta k^2 (theta from Eq. 14).  The phase shift over the
+    run is a quarter wave, so a sign error, a dropped factor 2 or a missing
+    term each move it by at least pi/4."""
+    n, tau_T, u0, A = 64, 0.8, 0.04, 0.1
+    k = 2 * math.pi / n
+    theta = (2 * tau_T - 1) / 4
+    m = np.zeros((1, n), np.uint8)
+    s = O.State(O.mask_geom(n, 1, 1, 1), O.make_params(tau=0.8, tau_T=tau_T), m)
+    x = np.arange(n)
+    T = 1.0 + A * np.sin(k * x)
+    for c in range(n):
+        s.f[:, c] = O.feq(0.0, u0, 0.0)
+    EXT, EYT = np.array([1, 0, -1, 0]), np.array([0, 1, 0, -1])
+    s.T[:] = 0.25 * T[None, :] * (1 + 2 * (EXT[:, None] * u0 + EYT[:, None] * 0.0))
+
+    def amp():
+        _, _, Tf = s.fields()
+        return np.sum((Tf - 1.0) * np.exp(-1j * k * x))
+
+    s.run(100)
+    a1 = amp()
+    t = 400  # u0 t = 16 cells: a quarter wave
+    s.run(t)
+    a2 = amp()
+    shift = -np.angle(a2 / a1)
+    assert shift == pytest.approx(k * u0 * t, rel=1e-2)
+    rate = -math.log(abs(a2 / a1)) / (t * k * k)
+    assert rate == pytest.approx(theta, rel=2e-2)
+    u, _, _ = s.fields()
+    assert np.abs(u[0] - u0).max() < 1e-15 and np.abs(u[1]).max() < 1e-15
+
+
+def test_thermal_inlet_and_outlet_rules_still_column():
+    """Thermal boundary rules with no flow: the inlet holds T_in at its
+    half link (anti-bounce-back, -T* + T_in/2) and the outlet has zero
+    gradient (-T* + T(x)/2, the cell's own T).  From T = 0 the deficit
+    T_in - T of a column of L cells then decays in the slowest mode of a
+    Dirichlet-Neumann slab, sin(pi xi / 2L) e^{-theta (pi/2L)^2 t} with xi the
+    distance from the inlet's half link.  An outlet that held a fixed
+    temperature would decay four times faster in sin(pi xi / L)."""
+    L, tau_T = 32, 1.0
+    theta = (2 * tau_T - 1) / 4
+    m, d = W.darcy_column(L, 0, 0, 1)
+    g = O.mask_geom(d["nx"], d["ny"], d["periodic_x"], d["periodic_y"], d["inlet_dir"],
+                    d["inlet_profile"], d["inlet_lo"], d["inlet_width"])
+    P = O.make_params(tau=0.8, tau_T=tau_T, T_in=1.0, T_hot=0.3, T_cold=0.6, T0=0.0)
+    s = O.State(g, P, m)
+    xi = np.arange(1, L + 1) - 0.5
+
+    def deficit():
+        return 1.0 - s.fields()[2][1:L + 1]
+
+    s.run(3000)
+    w1 = deficit()
+    s.run(2000)
+    w2 = deficit()
+    lam = -math.log(w2.max() / w1.max()) / 2000
+    assert lam == pytest.approx(theta * (math.pi / (2 * L)) ** 2, rel=2e-2)
+    shape = np.sin(math.pi * xi / (2 * L))
+    assert np.abs(w2 / w2.max() - shape).max() < 1e-2
+    assert np.argmax(w2) == L - 1  # the deficit peaks at the outlet end
+
+
+def test_thermal_inlet_and_outlet_rules_through_flow():
+    """Plug inflow at T_in through a column to the pressure outlet: the
+    uniform state f = feq(p_out, u_in), T_i = (T_in/4)(1 + 2 e_i.u_in) is a
+    fixed point of the inlet rule (moving-wall bounce-back and -T* + T_in/2),
+    the bulk and the outlet rules (pressure anti-bounce-back and the
+    zero-gradient -T* + T(x)/2), so the column settles at T = T_in exactly.
+    An outlet that bounced heat back, or an inlet that imposed another
+    temperature, would not."""
+    m, d = W.darcy_column(24, 0, 8, 1)
+    g = O.mask_geom(d["nx"], d["ny"], d["periodic_x"], d["periodic_y"], d["inlet_dir"],
+                    d["inlet_profile"], d["inlet_lo"], d["inlet_width"])
+    P = O.make_params(tau=0.8, tau_T=0.9, T_in=0.7, T_hot=1.0, T_cold=0.0, T0=0.2,
+                      u_in_max=0.02)
+    s = O.State(g, P, m)
+    s.run(40000)
+    u, p, T = s.fields()
+    act = m.reshape(-1) <= O.POROUS
+    assert np.abs(T[act] - 0.7).max() < 1e-12
+    assert np.abs(u[0][act] - 0.02).max() < 1e-12
+    assert np.abs(p[act]).max() < 1e-12
