@@ -306,11 +306,20 @@ def run_gpu(args):
             traffic = tr["dram_bytes_per_step"] * steps_per_launch
     except Exception:
         pass
+    studies = None
+    if rank == 0 and world == 1 and not args.no_studies:
+        dom.close()
+        torch.cuda.empty_cache()
+        studies = side_studies(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups_cpu, steps_cpu, cores, dt = oracle_sample(seconds_budget=12.0)
+        mlups_1, steps_1, _, dt_1 = oracle_sample(seconds_budget=4.0, threads=1)
         cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{steps_cpu} time steps of the 4096x2048 eye ({dt:.1f} s, FP64, OpenMP rows)"}
+               "sample": f"{steps_cpu} time steps of the 4096x2048 eye ({dt:.1f} s, FP64, OpenMP rows)",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": mlups_1, "unit": "MLUPS", "cores": 1,
+                                 "sample": f"{steps_1} time steps of the same eye ({dt_1:.1f} s)"}}
     if rank == 0:
         line = {
             "metric": "coupled MLUPS (active cells)", "value": value, "unit": "MLUPS",
@@ -338,12 +347,85 @@ def run_gpu(args):
             # single launches), the observing step and the finalize kernel
             "gpu_launches": args.steps * (3 if flow else CHECK + 1),
             "clocks": clk,
+            "studies": studies,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     dom.close()
     return 0
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def side_studies(dev) -> dict:
+    """Short measurements of the other forms, reported beside the headline
+    (they do not enter `value`): 16-bit deviation storage on the 8192 x 4096
+    eye (three check intervals per storage, eight-cell tile rows) and the
+    64-instance FP32 batch (three check intervals).  A few seconds."""
+    import torch
+
+    from paper_2102_12663_gb300 import lbm
+    from paper_2102_12663_gb300 import workloads as W
+    peak, _ = hbm_peak()
+    out = {}
+    cfg = W.CONFIG_PRECISION
+    for prec in ("f16", "bf16"):
+        st = torch.cuda.Stream(device=dev)
+        d = lbm.Domain(dict(nx=cfg["nx"], ny=cfg["ny"], angle_deg=cfg["angle_deg"]), precision=prec,
+                       device=dev, stream=st)
+        d.set_launch(**VEC16_LAUNCH)
+        d.set_params(W.config_params(cfg))
+        with torch.cuda.stream(st):
+            _time_intervals(d, 2)
+            ms = _time_intervals(d, 3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            d.step(100)
+            e1.record(st)
+            e1.synchronize()
+            kus = e0.elapsed_time(e1) / 100 * 1e3
+        n_act = d.info()["n_active"]
+        gbs = d.step_bytes() / (kus * 1e-6) / 1e9
+        out[f"{prec}_{cfg['nx']}x{cfg['ny']}"] = {
+            "mlups": n_act * CHECK * 3 / (ms * 1e-3) / 1e6, "step_kernel_us": kus, "gbs": gbs,
+            "hbm_frac": gbs / peak, "bytes_per_active_cell": d.step_bytes() / n_act,
+            "launch": VEC16_LAUNCH}
+        d.close()
+        del d
+        torch.cuda.empty_cache()
+    st = torch.cuda.Stream(device=dev)
+    doms = []
+    for inst in W.batch_instances(64):
+        d = lbm.Domain(dict(nx=inst["nx"], ny=inst["ny"], angle_deg=inst["angle_deg"]),
+                       precision="f32", device=dev, stream=st)
+        d.set_launch(**STUDY_LAUNCH)
+        d.set_params(inst["params"])
+        doms.append(d)
+    b = lbm.Batch("f32", max_instances=64, max_tiles=1 << 21, launch=STUDY_LAUNCH, stream=st)
+    for d in doms:
+        b.add(d)
+    with torch.cuda.stream(st):
+        _time_intervals(b, 2, batch=True)
+        ms = _time_intervals(b, 3, batch=True)
+    cells = b.active_cells()
+    out["batch_64_fp32"] = {"mlups": cells * CHECK * 3 / (ms * 1e-3) / 1e6,
+                            "hbm_frac": b.step_bytes() * CHECK * 3 / (ms * 1e-3) / 1e9 / peak,
+                            "active_cells": cells, "launch": STUDY_LAUNCH}
+    b.close()
+    for d in doms:
+        d.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # the FP32 4096 x 2048 line: 64 x 4 tiles, one graph-replayed launch per step
@@ -353,6 +435,8 @@ LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepp
               sweep_lag=0)
 # the studies (other grid sizes and many small grids): one launch per step
 STUDY_LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
+# 16-bit storages: 256-cell tile rows, eight cells per thread
+VEC16_LAUNCH = dict(tile_w=256, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):
@@ -586,6 +670,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the short 16-bit storage and batch measurements of the default line")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: run this many single fused steps of the "
                          "workload (no timing, no JSON line) and exit")

@@ -186,7 +186,10 @@ typedef struct lbm_observables {
 /* Launch shape of the fused step kernel: tiles of tile_w x (block_rows *
  * rows_per_thread) cells, one thread per column (FP64) or column pair (other
  * storages) and row group.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
- * <= 256, tile area >= 128 cells.
+ * <= 256, tile area >= 128 cells.  The 16-bit storages with tile_w 256 take
+ * eight columns per thread instead (32 threads per row, block_rows <= 8):
+ * rows whose cells are all away from boundaries then move each population
+ * plane as one 16-byte vector of eight cells.
  *
  * stepping selects how lbm_step advances a domain (the zero default is one
  * launch per step; the dataflow launch is faster where the per-step launch
@@ -441,8 +444,11 @@ void lbm_batch_destroy(lbm_batch* b);
  * rows x 12 doubles (about 0.8 MB), held by every GPU that loads the library
  * until the process exits.  The first call on a device looks up that array's
  * device address with the device current; make that first call before any
- * stream capture.  A grid with more than LBM_NOALLOC_MAX_ROWS rows is
- * rejected with LBM_EINVAL.  All calls on one device share the array and it
+ * stream capture.  The device current at the call must be the one that was
+ * current when the domain was created, else the call returns LBM_EINVAL.  A
+ * batch member may be read: while it belongs to a batch its work runs on the
+ * batch's stream, so the read follows the batch's steps.  A grid with more
+ * than LBM_NOALLOC_MAX_ROWS rows is rejected with LBM_EINVAL.  All calls on one device share the array and it
  * keeps the last call's contents: calls that overlap on the GPU (for example
  * on two streams with no ordering between them) race on it, calls on one
  * stream do not.  Synchronises the domain's stream. */

@@ -37,9 +37,10 @@
 #ifndef LBM_FLOW_MIN_BLOCKS
 #define LBM_FLOW_MIN_BLOCKS 3
 #endif
-// the same for the 16-bit storages (which convert on every load and store)
+// the 16-bit storages: 2 (128 registers), for the eight-cell vector path,
+// which keeps 13 planes of eight packed codes live
 #ifndef LBM_STEP_MIN_BLOCKS_16
-#define LBM_STEP_MIN_BLOCKS_16 3
+#define LBM_STEP_MIN_BLOCKS_16 2
 #endif
 
 namespace lbm {
@@ -316,8 +317,18 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     const E usq = ux * ux + uy * uy;
     const E S0 = E(K_W0) * (E(-1.5) * usq);
     const E sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    // p = [sum_{i>=1} f_i + S_0(u)] / (4 sigma); the FP32 form multiplies by 0.6
-    const E p = sizeof(R) == 8 ? (sum18 + S0) / E(4.0 * K_SIGMA) : (sum18 + S0) * E(0.6);
+    // p = [sum_{i>=1} f_i + S_0(u)] / (4 sigma); the FP32 form multiplies by 0.6.
+    // Pressure parts of feq_1..8: lambda p (axis) and gamma p (diagonal).  In
+    // FP64 they are formed from p as Eq. 7 writes them.  In FP32 (whose
+    // rounded constants 0.6, 1/3 and 1/12 all lie above the exact values) they
+    // are formed from P4 = 4 sigma p = sum18 + S_0: lambda p = P4 / 5, and
+    // gamma p = P4 / 4 - lambda p, an exact subtraction (Sterbenz), so the
+    // eight parts add up to P4 exactly.
+    const E P4 = sum18 + S0;
+    const E p = sizeof(R) == 8 ? P4 / E(4.0 * K_SIGMA) : P4 * E(0.6);
+    const E pax = sizeof(R) == 8 ? E(K_LAMBDA) * p : P4 * E(0.2);
+    const E pdg = sizeof(R) == 8 ? E(K_GAMMA) * p : P4 * E(0.25) - pax;
+    // T - Tref (Eq. 13 on the stored deviations; Tref = 0 for FP64)
     const E Tm = g[0] + g[1] + g[2] + g[3];
 
     // e_i . u for i = 0..8
@@ -334,11 +345,11 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
 
     // equilibrium, Eqs. 7-8
     E feq[9];
-    feq[0] = E(-4.0 * K_SIGMA) * p + S0;
+    feq[0] = (sizeof(R) == 8 ? E(-4.0 * K_SIGMA) * p : -P4) + S0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const E Si = E(wgt(i)) * (E(3.0) * eu[i] + E(4.5) * eu[i] * eu[i] - E(1.5) * usq);
-        feq[i] = (i <= 4 ? E(K_LAMBDA) : E(K_GAMMA)) * p + Si;
+        feq[i] = (i <= 4 ? pax : pdg) + Si;
     }
 
     // neighbour types (only next to a boundary)
@@ -417,7 +428,7 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     }
 
     // ---- body force, Eqs. 15-17: F_i = (1/2) e_i . F on the axis links --------
-    const E gb = E(ph.g_beta) * (Tm - E(ph.T0));
+    const E gb = E(ph.g_beta) * (Tm - E(ph.dT0));
     const E Fx = E(ph.drive_x) - gb * E(ph.gx);
     const E Fy = E(ph.drive_y) - gb * E(ph.gy);
     const E F1 = E(0.5) * Fx, F2 = E(0.5) * Fy;
@@ -425,8 +436,21 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     // ---- flow collision, Eq. 6 --------------------------------------------
     const E om = E(ph.omega);
     E fs[9];
+    if constexpr (sizeof(R) == 8) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fs[i] = f[i] - om * (f[i] - feq[i]);
+        for (int i = 0; i < 9; ++i) fs[i] = f[i] - om * (f[i] - feq[i]);
+    } else {
+        // FP32: the mean of the rounded non-equilibrium parts f_i - feq_i
+        // (zero in exact arithmetic) is taken out, so that the rounded
+        // equilibrium adds no mass (the pair path does the same)
+        E nq[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) nq[i] = f[i] - feq[i];
+        const E nm = (((nq[1] + nq[3]) + (nq[2] + nq[4])) + ((nq[5] + nq[7]) + (nq[6] + nq[8]))) * E(0.125);
+        fs[0] = f[0] - om * (f[0] - feq[0]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fs[i] = f[i] - om * (nq[i] - nm);
+    }
     fs[1] = fs[1] + F1;
     fs[2] = fs[2] + F2;
     fs[3] = fs[3] + (-F1);
@@ -455,10 +479,23 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     const E omT = E(ph.omegaT);
     const E Tq = E(0.25) * Tm;
     E gs[4];
+    if constexpr (sizeof(R) == 8) {
 #pragma unroll
-    for (int i = 1; i <= 4; ++i) {
-        const E teq = Tq * (E(1.0) + E(2.0) * eu[i]);
-        gs[i - 1] = g[i - 1] - omT * (g[i - 1] - teq);
+        for (int i = 1; i <= 4; ++i) {
+            const E teq = Tq * (E(1.0) + E(2.0) * eu[i]);
+            gs[i - 1] = g[i - 1] - omT * (g[i - 1] - teq);
+        }
+    } else {
+        // FP32, on the deviations from Tref/4: T_i^eq - Tref/4 =
+        // (T - Tref)/4 + (T/2) e_i.u; the mean of the rounded non-equilibrium
+        // parts is taken out, so that the rounded equilibrium adds no heat
+        const E Th = E(0.5) * (Tm + E(ph.Tref));
+        E nt[4];
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) nt[i - 1] = g[i - 1] - (Tq + Th * eu[i]);
+        const E mt = ((nt[0] + nt[2]) + (nt[1] + nt[3])) * E(0.25);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gs[i] = g[i] - omT * (nt[i] - mt);
     }
 
     const bool write = !OBS || (mode & OBS_WRITE);
@@ -524,9 +561,10 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
         E v = gs[i - 1];
         if (is_bnd) {
             const uint32_t tn = (ntypes >> (4 * (i - 1))) & 15u;
-            if (tn == COLD) v = -gs[i - 1] + E(0.5) * E(ph.T_cold);
-            else if (tn == HOT) v = -gs[i - 1] + E(0.5) * E(ph.T_hot);
-            else if (tn == INLET) v = -gs[i - 1] + E(0.5) * E(ph.T_in);
+            // anti-bounce-back of the deviations: T_w - Tref at the wall
+            if (tn == COLD) v = -gs[i - 1] + E(0.5) * (E(ph.T_cold) - E(ph.Tref));
+            else if (tn == HOT) v = -gs[i - 1] + E(0.5) * (E(ph.T_hot) - E(ph.Tref));
+            else if (tn == INLET) v = -gs[i - 1] + E(0.5) * (E(ph.T_in) - E(ph.Tref));
             else if (tn == OUTLET) v = -gs[i - 1] + E(0.5) * Tm;
             // adiabatic: bounce-back, zero heat flux
         }
@@ -570,34 +608,56 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const Ph
     const float ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     const float uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     const float usq = ux * ux + uy * uy;
-    const float S0 = float(K_W0) * (-1.5f * usq);
-    const float sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    const float p = (sum18 + S0) * 0.6f;
-    const float Tm = f[9] + f[10] + f[11] + f[12];
-    const float om = ph.omega;
-    // equilibrium per opposite pair: common = kappa p + w (4.5 eu^2 - 1.5 usq), odd = 3 w eu
-    const float c_ax = float(K_LAMBDA) * p - float(1.5 * K_W1) * usq;
-    const float c_dg = float(K_GAMMA) * p - float(1.5 * K_W5) * usq;
     const float e5 = ux + uy, e6 = uy - ux;
-    const float q1 = c_ax + float(4.5 * K_W1) * ux * ux, o1 = float(3.0 * K_W1) * ux;
-    const float q2 = c_ax + float(4.5 * K_W1) * uy * uy, o2 = float(3.0 * K_W1) * uy;
-    const float q5 = c_dg + float(4.5 * K_W5) * e5 * e5, o5 = float(3.0 * K_W5) * e5;
-    const float q6 = c_dg + float(4.5 * K_W5) * e6 * e6, o6 = float(3.0 * K_W5) * e6;
-    const float feq0 = float(-4.0 * K_SIGMA) * p + S0;
+    // even parts w_i (4.5 (e_i.u)^2 - 1.5 |u|^2) of S_i, one per opposite pair
+    const float h1 = float(4.5 * K_W1) * ux * ux - float(1.5 * K_W1) * usq;
+    const float h2 = float(4.5 * K_W1) * uy * uy - float(1.5 * K_W1) * usq;
+    const float h5 = float(4.5 * K_W5) * e5 * e5 - float(1.5 * K_W5) * usq;
+    const float h6 = float(4.5 * K_W5) * e6 * e6 - float(1.5 * K_W5) * usq;
+    // S_0 = -sum_{i>=1} S_i (the S_i of Eq. 8 sum to zero), from the rounded even parts
+    const float S0 = -2.0f * ((h1 + h2) + (h5 + h6));
+    const float sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    // pressure parts lambda p = P4 / 5 and gamma p = P4 / 20 of P4 = 4 sigma p
+    // (Eq. 9); gamma p = P4 / 4 - lambda p is exact (Sterbenz), so the eight
+    // pressure parts add up to P4 exactly
+    const float P4 = sum18 + S0;
+    const float pax = P4 * 0.2f;
+    const float pdg = P4 * 0.25f - pax;
+    const float Tm = f[9] + f[10] + f[11] + f[12];  // T - Tref (stored deviations)
+    const float om = ph.omega;
+    // equilibrium per opposite pair: common = kappa p + even part, odd = 3 w eu
+    const float q1 = pax + h1, o1 = float(3.0 * K_W1) * ux;
+    const float q2 = pax + h2, o2 = float(3.0 * K_W1) * uy;
+    const float q5 = pdg + h5, o5 = float(3.0 * K_W5) * e5;
+    const float q6 = pdg + h6, o6 = float(3.0 * K_W5) * e6;
+    const float feq0 = -P4 + S0;
     // body force F = drive - g beta (T - T0) g_hat; F_i = (1/2) e_i . F on the axis links
-    const float gb = ph.g_beta * (Tm - ph.T0);
+    const float gb = ph.g_beta * (Tm - ph.dT0);
     const float Fx = ph.drive_x - gb * ph.gx;
     const float Fy = ph.drive_y - gb * ph.gy;
     const float F1 = 0.5f * Fx, F2 = 0.5f * Fy;
+    // Non-equilibrium parts n_i = f_i - feq_i (exact subtractions: f_i and
+    // feq_i are close).  Their sum vanishes in exact arithmetic (the
+    // equilibrium carries the cell's mass sum_{i>=1} f_i, Eq. 9), but the
+    // rounded equilibrium misses it by a few units in the last place of the
+    // populations, with a bias that survives the sum over cells and steps: a
+    // mass source whose steady outflow raises the IOP.  So the mean of the
+    // rounded n_i is taken out before the relaxation; what remains of the
+    // collision's mass error is the final rounding of each f_i.
+    const float n1 = f[1] - (q1 + o1), n3 = f[3] - (q1 - o1);
+    const float n2 = f[2] - (q2 + o2), n4 = f[4] - (q2 - o2);
+    const float n5 = f[5] - (q5 + o5), n7 = f[7] - (q5 - o5);
+    const float n6 = f[6] - (q6 + o6), n8 = f[8] - (q6 - o6);
+    const float nm = (((n1 + n3) + (n2 + n4)) + ((n5 + n7) + (n6 + n8))) * 0.125f;
     f[0] = f[0] - om * (f[0] - feq0);
-    f[1] = f[1] - om * (f[1] - (q1 + o1)) + F1;
-    f[3] = f[3] - om * (f[3] - (q1 - o1)) - F1;
-    f[2] = f[2] - om * (f[2] - (q2 + o2)) + F2;
-    f[4] = f[4] - om * (f[4] - (q2 - o2)) - F2;
-    f[5] = f[5] - om * (f[5] - (q5 + o5));
-    f[7] = f[7] - om * (f[7] - (q5 - o5));
-    f[6] = f[6] - om * (f[6] - (q6 + o6));
-    f[8] = f[8] - om * (f[8] - (q6 - o6));
+    f[1] = f[1] - om * (n1 - nm) + F1;
+    f[3] = f[3] - om * (n3 - nm) - F1;
+    f[2] = f[2] - om * (n2 - nm) + F2;
+    f[4] = f[4] - om * (n4 - nm) - F2;
+    f[5] = f[5] - om * (n5 - nm);
+    f[7] = f[7] - om * (n7 - nm);
+    f[6] = f[6] - om * (n6 - nm);
+    f[8] = f[8] - om * (n8 - nm);
     if (porous) {
         const float umx = (ux + 0.5f * Fx) / ph.den;
         const float umy = (uy + 0.5f * Fy) / ph.den;
@@ -612,11 +672,17 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const Ph
         f[6] += a5 * (FDy - FDx);
         f[8] -= a5 * (FDy - FDx);
     }
-    const float omT = ph.omegaT, Tq = 0.25f * Tm;
-    f[9] = f[9] - omT * (f[9] - Tq * (1.0f + 2.0f * ux));
-    f[10] = f[10] - omT * (f[10] - Tq * (1.0f + 2.0f * uy));
-    f[11] = f[11] - omT * (f[11] - Tq * (1.0f - 2.0f * ux));
-    f[12] = f[12] - omT * (f[12] - Tq * (1.0f - 2.0f * uy));
+    // heat: the same for the D2Q4 populations, whose equilibria carry T.  They
+    // are stored and collided as deviations from Tref/4, so their rounding is
+    // that of T - Tref: T_i^eq - Tref/4 = (T - Tref)/4 + (T/2) e_i.u
+    const float omT = ph.omegaT, Tq = 0.25f * Tm, Th = 0.5f * (Tm + ph.Tref);
+    const float m1 = f[9] - (Tq + Th * ux), m3 = f[11] - (Tq - Th * ux);
+    const float m2 = f[10] - (Tq + Th * uy), m4 = f[12] - (Tq - Th * uy);
+    const float mm = ((m1 + m3) + (m2 + m4)) * 0.25f;
+    f[9] = f[9] - omT * (m1 - mm);
+    f[10] = f[10] - omT * (m2 - mm);
+    f[11] = f[11] - omT * (m3 - mm);
+    f[12] = f[12] - omT * (m4 - mm);
 }
 
 // Collision of a cell pair (cells x and x+1, 13 values each) and its AA-pattern
@@ -817,12 +883,190 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
     pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
 }
 
+// ---------------------------------------------------------------------------
+// Interior path of the 16-bit storages on 256-cell tile rows: one lane updates
+// eight neighbouring cells x0 .. x0 + 7 (x0 a multiple of 8), and every plane
+// moves as one 16-byte vector of eight packed 16-bit codes, i.e. 13 vector
+// loads and 13 vector stores per eight cells.  The codes stay packed in
+// registers (w[plane][word], two codes per 32-bit word, the lower column in
+// the low half), and the two cells of a word are decoded, collided and
+// encoded together, their results replacing the word they came from, so only
+// two cells' 13 values are live as FP32 at a time.  On an odd step the
+// x-shifted links are assembled from the neighbouring lane's words (one
+// shuffle per plane and __byte_perm), and the warp's first and last lanes
+// load or store the one code outside the warp's 256 cells.  Same model and
+// arithmetic as the pair path (collide_interior).
+
+// the code pair (b of lo, a of hi): word whose low half is the high half of
+// lo and whose high half is the low half of hi (a one-code shift)
+__device__ __forceinline__ uint32_t shift_pair(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x5432); }
+
+template <class ST, int PAR>
+__device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0, int y, uint32_t por) {
+    using T = typename ST::T;
+    static_assert(sizeof(T) == 2, "16-bit storages only");
+    const int nx = d.nx, ny = d.ny;
+    const int np = (int)d.npad;
+    T* const P = static_cast<T*>(d.pops);
+    const int lane = threadIdx.x & 31;
+    const int row = y * nx;
+    const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
+    const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;          // column left of the lane's cells
+    const int xr = x0 + VEC16_CELLS == nx ? 0 : x0 + VEC16_CELLS;  // column right of them
+    uint32_t w[13][4];
+
+    // ---- load -------------------------------------------------------------
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        if (PAR == 0 || k == 0) {
+            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(P + k * np + row + x0));
+            w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+        } else {
+            const bool heat = k > 8;
+            const int i = heat ? k - 8 : k;             // lattice direction
+            const int pl = heat ? 8 + opp(i) : opp(i);  // f_i(x) sits in slot (x - e_i, opp(i))
+            const int sr = ey(i) == 1 ? rowd : (ey(i) == -1 ? rowu : row);
+            const T* src = P + pl * np + sr;
+            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(src + x0));
+            if (ex(i) == 0) {
+                w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+            } else if (ex(i) == 1) {  // source columns x0 - 1 .. x0 + 6
+                uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+                if (lane == 0) prev = (uint32_t)__ldcg(reinterpret_cast<const unsigned short*>(src + xl)) << 16;
+                w[k][0] = shift_pair(prev, v.x);
+                w[k][1] = shift_pair(v.x, v.y);
+                w[k][2] = shift_pair(v.y, v.z);
+                w[k][3] = shift_pair(v.z, v.w);
+            } else {                  // source columns x0 + 1 .. x0 + 8
+                uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+                if (lane == 31) next = (uint32_t)__ldcg(reinterpret_cast<const unsigned short*>(src + xr));
+                w[k][0] = shift_pair(v.x, v.y);
+                w[k][1] = shift_pair(v.y, v.z);
+                w[k][2] = shift_pair(v.z, v.w);
+                w[k][3] = shift_pair(v.w, next);
+            }
+        }
+    }
+
+    // ---- collide, two cells (one packed word per plane) at a time -----------
+    // w[k] holds the inputs of direction k (even step: slot k = plane k; odd
+    // step: assembled from plane opp(k)); the result of direction k goes to
+    // plane opp(k) of the cells' own columns on an even step and to plane k,
+    // shifted by e_k, on an odd step.  Each pass takes word 0 of every plane
+    // (cells 2q and 2q + 1) and moves the result word to the back, so after
+    // four passes every plane's words are the results in their own places.
+    // The pass is not unrolled: every register index stays static, and the
+    // loop body (two inlined collisions) stays small enough for the
+    // instruction cache.
+#pragma unroll 1
+    for (int q = 0; q < VEC16_CELLS / 2; ++q) {
+        float a[13], b[13];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 v = ST::decf2(w[k][0], d);
+            a[k] = v.x;
+            b[k] = v.y;
+        }
+#pragma unroll
+        for (int k = 9; k < 13; ++k) {
+            const float2 v = ST::decT2(w[k][0], d);
+            a[k] = v.x;
+            b[k] = v.y;
+        }
+        collide_interior(a, ((por >> (2 * q)) & 1u) != 0, d.pf);
+        collide_interior(b, ((por >> (2 * q + 1)) & 1u) != 0, d.pf);
+        uint32_t o[13];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            const int dst = PAR == 0 ? (k < 9 ? opp(k) : 8 + opp(k - 8)) : k;
+            o[dst] = k < 9 ? ST::encf2(a[k], b[k], d) : ST::encT2(a[k], b[k], d);
+        }
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            w[k][0] = w[k][1];
+            w[k][1] = w[k][2];
+            w[k][2] = w[k][3];
+            w[k][3] = o[k];
+        }
+    }
+
+    // ---- store ------------------------------------------------------------
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        if (PAR == 0 || k == 0) {
+            st_pol<ST::kPol>(reinterpret_cast<uint4*>(P + k * np + row + x0), make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]));
+            continue;
+        }
+        const bool heat = k > 8;
+        const int i = heat ? k - 8 : k;
+        const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);  // f*_i(x) goes to slot (x + e_i, i)
+        T* const dst = P + k * np + dr;
+        if (ex(i) == 0) {
+            st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]));
+        } else if (ex(i) == 1) {  // destination columns x0 + 1 .. x0 + 8
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, w[k][3], 1);
+            const uint4 o = make_uint4(shift_pair(prev, w[k][0]), shift_pair(w[k][0], w[k][1]),
+                                       shift_pair(w[k][1], w[k][2]), shift_pair(w[k][2], w[k][3]));
+            if (lane != 0) {
+                st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), o);
+            } else {  // column x0 belongs to the cell left of the warp
+                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + x0 + 1), (unsigned short)(o.x >> 16));
+                st_pol<ST::kPol>(reinterpret_cast<unsigned int*>(dst + x0 + 2), o.y);
+                st_pol<ST::kPol>(reinterpret_cast<uint2*>(dst + x0 + 4), make_uint2(o.z, o.w));
+            }
+            if (lane == 31)
+                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + xr), (unsigned short)(w[k][3] >> 16));
+        } else {                  // destination columns x0 - 1 .. x0 + 6
+            const uint32_t next = __shfl_down_sync(0xffffffffu, w[k][0], 1);
+            const uint4 o = make_uint4(shift_pair(w[k][0], w[k][1]), shift_pair(w[k][1], w[k][2]),
+                                       shift_pair(w[k][2], w[k][3]), shift_pair(w[k][3], next));
+            if (lane != 31) {
+                st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), o);
+            } else {  // column x0 + 7 belongs to the cell right of the warp
+                st_pol<ST::kPol>(reinterpret_cast<uint2*>(dst + x0), make_uint2(o.x, o.y));
+                st_pol<ST::kPol>(reinterpret_cast<unsigned int*>(dst + x0 + 4), o.z);
+                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + x0 + 6), (unsigned short)(o.w & 0xFFFFu));
+            }
+            if (lane == 0)
+                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + xl), (unsigned short)(w[k][0] & 0xFFFFu));
+        }
+    }
+}
+
+// One row of cell pairs (x, x + 1) of a warp that covers 64 consecutive
+// cells: the pair path where the whole warp's cells are interior, else the
+// general per-cell update.
+template <class ST, bool OBS, int PAR, class A>
+__device__ __forceinline__ void pair_row(const InstDesc& sd, int x, int y, bool pure, bool vec_ok, int mode,
+                                         A* acc) {
+    bool fast = false;
+    if (vec_ok) {
+        uint32_t m2 = 0u;
+        if (pure) {
+            fast = true;
+        } else {
+            const bool in = y < sd.ny && x + 1 < sd.nx;
+            if (in) m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x);
+            else m2 = 0xFFFFu;
+            // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
+            fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+        }
+        if (fast)
+            update_pair_interior<ST, PAR, OBS, A>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
+                                               (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode, acc);
+    }
+    if (!fast) {
+        if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
+        if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x + 1, y, mode, acc);
+    }
+}
+
 template <class ST, bool OBS, int PAR, class A = double>
-__device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, int rpt,
+__device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, const Shape& shape,
                                           A* acc) {
-    constexpr int V = sizeof(typename ST::R) == 4 ? 2 : 1;
-    const int x = te.z + V * threadIdx.x;
-    if constexpr (V == 2) {
+    const int rpt = shape.rpt;
+    if constexpr (sizeof(typename ST::R) == 4) {
         // the pair path needs whole warps on one row and even rows; an
         // observing step takes it too when it also writes (the steady-state
         // check), while observe-only reads stay on the per-cell path
@@ -830,31 +1074,47 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
         // a pure tile (every cell fluid, in the grid, away from boundaries)
         // takes the pair path without reading its mask
         const bool pure = (te.y & TILE_PURE) != 0;
-        for (int r = 0; r < rpt; ++r) {
-            const int y = te.w + threadIdx.y + r * blockDim.y;
-            bool fast = false;
-            if (vec_ok) {
-                uint32_t m2 = 0u;
-                if (pure) {
-                    fast = true;
-                } else {
-                    const bool in = y < sd.ny && x + 1 < sd.nx;
-                    if (in) m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x);
-                    else m2 = 0xFFFFu;
-                    // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
-                    fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+        if (sizeof(typename ST::T) == 2 && shape.tw == VEC16_TILE_W) {
+            // 16-bit storage, eight cells per lane (blockDim.x == 32): plain
+            // steps of rows whose 256 cells are all interior take the vector
+            // path; the others, and observing steps, take four 64-cell pair rows
+            const int x0 = te.z + VEC16_CELLS * threadIdx.x;
+            const bool v16_ok = !OBS && (sd.nx % VEC16_CELLS) == 0;
+            for (int r = 0; r < rpt; ++r) {
+                const int y = te.w + threadIdx.y + r * blockDim.y;
+                bool fast = false;
+                uint32_t por = 0u;
+                if constexpr (!OBS && sizeof(typename ST::T) == 2) {
+                    if (v16_ok) {
+                        if (pure) {
+                            fast = true;
+                        } else {
+                            uint64_t m8 = ~0ull;
+                            if (y < sd.ny && x0 + VEC16_CELLS <= sd.nx)
+                                m8 = __ldg(reinterpret_cast<const unsigned long long*>(sd.mask + (int64_t)y * sd.nx + x0));
+                            fast = __all_sync(0xffffffffu, (m8 & 0x0E0E0E0E0E0E0E0Eull) == 0ull);
+                            if (sd.tm_model == 0)
+#pragma unroll
+                                for (int j = 0; j < VEC16_CELLS; ++j) por |= (uint32_t)((m8 >> (8 * j)) & 1u) << j;
+                        }
+                        if (fast) update_vec16_interior<ST, PAR>(sd, x0, y, por);
+                    }
                 }
-                if (fast)
-                    update_pair_interior<ST, PAR, OBS, A>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
-                                                       (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode,
-                                                       acc);
+                if (!fast) {
+#pragma unroll 1
+                    for (int s = 0; s < VEC16_CELLS / 2; ++s)
+                        pair_row<ST, OBS, PAR, A>(sd, te.z + 64 * s + 2 * (int)threadIdx.x, y, pure, vec_ok, mode, acc);
+                }
             }
-            if (!fast) {
-                if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
-                if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x + 1, y, mode, acc);
+        } else {
+            const int x = te.z + 2 * threadIdx.x;
+            for (int r = 0; r < rpt; ++r) {
+                const int y = te.w + threadIdx.y + r * blockDim.y;
+                pair_row<ST, OBS, PAR, A>(sd, x, y, pure, vec_ok, mode, acc);
             }
         }
     } else {
+        const int x = te.z + threadIdx.x;
         for (int r = 0; r < rpt; ++r) {
             const int y = te.w + threadIdx.y + r * blockDim.y;
             if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
@@ -1322,8 +1582,8 @@ __global__ void __launch_bounds__(256, OBS ? 2 : step_min_blocks<ST>()) step_ker
         A acc[NPART];
 #pragma unroll
         for (int k = 0; k < NPART; ++k) acc[k] = A(0);
-        if (parity) tile_rows<ST, OBS, 1, A>(sd, te, mode, shape.rpt, acc);
-        else tile_rows<ST, OBS, 0, A>(sd, te, mode, shape.rpt, acc);
+        if (parity) tile_rows<ST, OBS, 1, A>(sd, te, mode, shape, acc);
+        else tile_rows<ST, OBS, 0, A>(sd, te, mode, shape, acc);
         if (OBS && (mode & OBS_STATS)) {
             warp_block_reduce<A>(acc, red, sd.partials + (int64_t)(te.y & TILE_INDEX) * NPART);
         }
@@ -1418,8 +1678,8 @@ __global__ void __launch_bounds__(256, flow_min_blocks<ST>())
         __syncthreads();
         const int parity = (sd.parity ^ fa.flip ^ s) & 1;
         double acc[NPART];
-        if (parity) tile_rows<ST, false, 1>(sd, te, 0, shape.rpt, acc);
-        else tile_rows<ST, false, 0>(sd, te, 0, shape.rpt, acc);
+        if (parity) tile_rows<ST, false, 1>(sd, te, 0, shape, acc);
+        else tile_rows<ST, false, 0>(sd, te, 0, shape, acc);
         __syncthreads();
         // a thread outside warp 0 reports, so that the release overlaps warp
         // 0's polls for the next item

@@ -147,6 +147,7 @@ struct lbm_domain {
     std::vector<uint8_t> hmask;  // cell types with near-boundary bits
     cudaStream_t stream = nullptr;
     int num_sms = 1;
+    int device = 0;              // CUDA device current at creation (the buffer's)
     char* base = nullptr;
     InstDesc h{};                // host copy of the device descriptor
     InstDesc* d_desc = nullptr;
@@ -174,6 +175,18 @@ struct lbm_domain {
     int64_t step = 0;
     double u_seep = 0.0;              // lumped TM: current seepage speed
     double last_iop = 0.0;            // IOP of the last steady-state check
+    // Pressure reference of the stored flow populations: the library stores
+    // f_i - kappa_i p_ref (kappa_0 = -4 sigma, lambda on the axes, gamma on the
+    // diagonals, Eq. 7) and runs the kernels with the outlet pressure
+    // p_out - p_ref.  Guo's incompressible model is invariant under this
+    // shift (every equilibrium, moment and boundary rule keeps its form with
+    // p - p_ref in place of p), so it changes only the size of the stored
+    // values: the steady-state loops move p_ref to the chamber pressure, and
+    // the rounding of FP32 and 16-bit populations then scales with the
+    // velocity and the pressure variation instead of the IOP.  Always 0 for
+    // FP64 (bit parity with a plain evaluation).
+    double p_ref = 0.0;
+    double pin_pref[2] = {0.0, 0.0};  // p_ref of the interval in each pinned slot
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
     std::vector<int4> htiles;         // host copy of the tile list
     std::vector<int> hnbr;            // host copy of the neighbour lists
@@ -187,10 +200,13 @@ struct lbm_domain {
 // plain steps captured per CUDA graph (even, so a replay returns to the same parity)
 static constexpr int GRAPH_STEPS = 32;
 
-static bool launch_ok(const lbm_launch& l) {
+// prec: the storage precision (it sets the cells each thread updates, hence
+// the threads of a block: at most 256)
+static bool launch_ok(const lbm_launch& l, int prec) {
     const bool tw_ok = l.tile_w == 32 || l.tile_w == 64 || l.tile_w == 128 || l.tile_w == 256;
-    return tw_ok && l.block_rows >= 1 && l.rows_per_thread >= 1 && l.rows_per_thread <= 64 &&
-           l.tile_w * l.block_rows <= 256 &&
+    const bool rows_ok = cells_per_thread(prec, l.tile_w) == VEC16_CELLS ? l.block_rows <= 256 / 32
+                                                                          : l.tile_w * l.block_rows <= 256;
+    return tw_ok && l.block_rows >= 1 && l.rows_per_thread >= 1 && l.rows_per_thread <= 64 && rows_ok &&
            (int64_t)l.tile_w * l.block_rows * l.rows_per_thread >= MIN_TILE_AREA &&
            l.blocks_per_sm >= 0 && l.blocks_per_sm <= 32 &&
            (l.stepping == LBM_STEP_FLOW || l.stepping == LBM_STEP_PER_LAUNCH) &&
@@ -430,7 +446,8 @@ __global__ void init_kernel(const InstDesc* __restrict__ dp, double noise_amp, u
         }
         const double Ti = 0.25 * (d.pd.T0 + noise);
         for (int i = 0; i < 9; ++i) ST::stf(P + i * d.npad + c, (typename ST::R)feq[i], d);
-        for (int i = 1; i <= 4; ++i) ST::stT(P + (8 + i) * d.npad + c, (typename ST::R)Ti, d);
+        // heat populations are stored as deviations from Tshift
+        for (int i = 1; i <= 4; ++i) ST::stT(P + (8 + i) * d.npad + c, (typename ST::R)(Ti - (double)d.Tshift), d);
     }
 }
 
@@ -449,8 +466,11 @@ __device__ __forceinline__ int64_t slot_of(const InstDesc& d, int x, int y, int 
     return (heat ? (8 + o) : o) * d.npad + (int64_t)ys * d.nx + xs;
 }
 
+// stored flow populations are f_i - kappa_i p_ref
+__device__ __forceinline__ double kappa(int i) { return i == 0 ? -4.0 * K_SIGMA : (i <= 4 ? K_LAMBDA : K_GAMMA); }
+
 template <class ST>
-__global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, double* __restrict__ f,
+__global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, double p_ref, double* __restrict__ f,
                                  double* __restrict__ g) {
     const InstDesc d = *dp;
     using T = typename ST::T;
@@ -464,7 +484,7 @@ __global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, do
         if (f) {
             double fv[9];
             for (int i = 0; i < 9; ++i)
-                fv[i] = act ? (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d) : 0.0;
+                fv[i] = act ? (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d) + kappa(i) * p_ref : 0.0;
             if (act && d.bouzidi && (m & CURVED)) {
                 const CurvedCell* ce = curved_entry(d, x, y);
                 if (ce) bouzidi_read<double>(ce, fv);
@@ -472,13 +492,15 @@ __global__ void read_pops_kernel(const InstDesc* __restrict__ dp, int parity, do
             for (int i = 0; i < 9; ++i) f[i * N + c] = fv[i];
         }
         for (int i = 1; i <= 4; ++i)
-            if (g) g[(i - 1) * N + c] = act ? (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d) : 0.0;
+            if (g)
+                g[(i - 1) * N + c] =
+                    act ? (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d) + (double)d.Tshift : 0.0;
     }
 }
 
 template <class ST>
-__global__ void write_pops_kernel(const InstDesc* __restrict__ dp, int parity, const double* __restrict__ f,
-                                  const double* __restrict__ g) {
+__global__ void write_pops_kernel(const InstDesc* __restrict__ dp, int parity, double p_ref,
+                                  const double* __restrict__ f, const double* __restrict__ g) {
     const InstDesc d = *dp;
     using T = typename ST::T;
     using R = typename ST::R;
@@ -501,16 +523,40 @@ __global__ void write_pops_kernel(const InstDesc* __restrict__ dp, int parity, c
                     if (q < 0.5) fv[opp(i)] = (fv[opp(i)] - (1.0 - 2.0 * q) * fv[i]) / (2.0 * q);
                 }
             }
-            for (int i = 0; i < 9; ++i) ST::stf(P + slot_of(d, x, y, i, parity, false), (R)fv[i], d);
+            for (int i = 0; i < 9; ++i)
+                ST::stf(P + slot_of(d, x, y, i, parity, false), (R)(fv[i] - kappa(i) * p_ref), d);
         }
         if (g)
-            for (int i = 1; i <= 4; ++i) ST::stT(P + slot_of(d, x, y, i, parity, true), (R)g[(i - 1) * N + c], d);
+            for (int i = 1; i <= 4; ++i)
+                ST::stT(P + slot_of(d, x, y, i, parity, true), (R)(g[(i - 1) * N + c] - (double)d.Tshift), d);
+    }
+}
+
+// Moves the pressure reference of the stored flow populations by dp: every
+// population of an active cell (found in its slot at this parity) loses
+// kappa_i dp.  The q < 1/2 completion of the curved cornea interpolates two
+// slots with weights that add up to 1, so it shifts alike.
+template <class ST>
+__global__ void shift_pressure_kernel(const InstDesc* __restrict__ dp, int parity, double dpr) {
+    const InstDesc d = *dp;
+    using T = typename ST::T;
+    using R = typename ST::R;
+    T* P = static_cast<T*>(d.pops);
+    const int64_t N = (int64_t)d.nx * d.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if ((d.mask[c] & TYPE_BITS) > POROUS) continue;
+        const int x = (int)(c % d.nx), y = (int)(c / d.nx);
+        for (int i = 0; i < 9; ++i) {
+            T* q = P + slot_of(d, x, y, i, parity, false);
+            ST::stf(q, (R)((double)ST::ldf(q, d) - kappa(i) * dpr), d);
+        }
     }
 }
 
 // Eq. 9 and Eq. 13 in FP64 on the stored populations
 template <class ST>
-__global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, double* __restrict__ u,
+__global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, double p_ref, double* __restrict__ u,
                               double* __restrict__ p, double* __restrict__ Tf) {
     const InstDesc d = *dp;
     using T = typename ST::T;
@@ -524,7 +570,8 @@ __global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, doubl
             const int x = (int)(c % d.nx), y = (int)(c / d.nx);
             double fv[9], gv[4];
             for (int i = 0; i < 9; ++i) fv[i] = (double)ST::ldf(P + slot_of(d, x, y, i, parity, false), d);
-            for (int i = 1; i <= 4; ++i) gv[i - 1] = (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d);
+            for (int i = 1; i <= 4; ++i)
+                gv[i - 1] = (double)ST::ldT(P + slot_of(d, x, y, i, parity, true), d) + (double)d.Tshift;
             if (d.bouzidi && (d.mask[c] & CURVED)) {
                 const CurvedCell* ce = curved_entry(d, x, y);
                 if (ce) bouzidi_read<double>(ce, fv);
@@ -534,7 +581,7 @@ __global__ void fields_kernel(const InstDesc* __restrict__ dp, int parity, doubl
             const double usq = ux * ux + uy * uy;
             const double S0 = K_W0 * (-1.5 * usq);
             const double s = fv[1] + fv[2] + fv[3] + fv[4] + fv[5] + fv[6] + fv[7] + fv[8];
-            pp = (s + S0) / (4.0 * K_SIGMA);
+            pp = (s + S0) / (4.0 * K_SIGMA) + p_ref;
             TT = gv[0] + gv[1] + gv[2] + gv[3];
         }
         if (u) { u[c] = ux; u[N + c] = uy; }
@@ -746,6 +793,7 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
         delete d;
         return fail(LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
     }
+    d->device = dev;
     d->d_desc = reinterpret_cast<InstDesc*>(d->base + d->L.desc);
     d->d_obs = reinterpret_cast<double*>(d->base + d->L.obs);
     d->d_tiles = reinterpret_cast<int4*>(d->base + d->L.tiles);
@@ -853,6 +901,36 @@ static bool finite_all(const lbm_params& p) {
 static void update_seepage(lbm_domain* d, double iop);
 
 // validates p and derives the descriptor's parameter fields (no upload)
+// Reference of the stored heat deviations in both parameter blocks: Tref =
+// 4 Tshift (fixed when the state is initialised), dT0 = T0 - Tref.
+static void sync_heat_reference(lbm_domain* d) {
+    const double Tref = 4.0 * (double)d->h.Tshift;
+    d->h.pd.Tref = Tref;
+    d->h.pd.dT0 = d->params.T0 - Tref;
+    d->h.pf.Tref = (float)Tref;
+    d->h.pf.dT0 = (float)(d->params.T0 - Tref);
+}
+
+// Heat encoding fixed at initialisation: every storage but FP64 holds T_i -
+// T0/4; the 16-bit storages hold it as companded 16-bit fixed point
+// (enc_tfix).  |T - T0| <= span for a temperature field between the wall,
+// inflow and reference temperatures, so |T_i - T0/4| <= span/4 near
+// equilibrium: the fine part of the code carries that with 10 % to spare,
+// plus the advective part (T/2) e.u of the equilibrium up to |u| = 0.04.
+// The coarse part reaches 3.67 times as far, past the 3/4 span that
+// anti-bounce-back can return while a boundary layer forms.
+static void set_heat_encoding(lbm_domain* d) {
+    const lbm_params& p = d->params;
+    d->h.Tshift = d->prec == LBM_F64 ? 0.0f : (float)(0.25 * p.T0);
+    const double span = std::max({std::fabs(p.T_cold - p.T0), std::fabs(p.T_hot - p.T0),
+                                  std::fabs(p.T_in - p.T0), std::fabs(p.noise_amp)});
+    const double tmax = std::max({std::fabs(p.T_cold), std::fabs(p.T_hot), std::fabs(p.T_in), std::fabs(p.T0)});
+    const double fine = 1.1 * 0.25 * span + 0.02 * tmax + 1e-6;
+    d->h.Tstep = (float)(fine / TFIX_KNEE);
+    d->h.Tscale = 1.0f / d->h.Tstep;
+    sync_heat_reference(d);
+}
+
 static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     if (!d || !p) return fail(LBM_EINVAL, "null argument");
     if (!finite_all(*p)) return fail(LBM_EINVAL, "non-finite parameter");
@@ -883,7 +961,7 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     const double nu = (2.0 * p->tau - 1.0) / 6.0;  // Eq. 10
     h.cK = nu / p->K_tm;
     h.den = 1.0 + 0.5 * h.cK;
-    h.p_out = p->p_out;
+    h.p_out = p->p_out - d->p_ref;  // kernels run relative to p_ref
     h.drive_x = p->drive[0];
     h.drive_y = p->drive[1];
     h.kwss = -(1.0 - 1.0 / (2.0 * p->tau));
@@ -907,6 +985,7 @@ static lbm_status apply_params(lbm_domain* d, const lbm_params* p) {
     h.u_seep = d->u_seep;
     f.u_seep = (float)d->u_seep;
     d->params = *p;
+    sync_heat_reference(d);
     return LBM_OK;
 }
 
@@ -931,8 +1010,11 @@ extern "C" lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
 extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
     if (!d) return fail(LBM_EINVAL, "null domain");
     if (!d->have_params) return fail(LBM_EINVAL, "set parameters before resetting the state");
-    const bool lowp = d->prec == LBM_F16DEV || d->prec == LBM_BF16DEV;
-    d->h.Tshift = lowp ? (float)(0.25 * d->params.T0) : 0.0f;
+    set_heat_encoding(d);
+    // the initial state f = feq(p_out, 0) is all zeros relative to p_ref = p_out
+    d->p_ref = d->prec == LBM_F64 ? 0.0 : d->params.p_out;
+    d->h.pd.p_out = d->params.p_out - d->p_ref;
+    d->h.pf.p_out = (float)d->h.pd.p_out;
     d->h.snap_valid = 0;
     d->h.parity = 0;
     d->u_seep = 0.0;
@@ -1090,16 +1172,20 @@ static lbm_status fetch_obs(lbm_domain* d, double* o) {
     return fail(LBM_ECUDA, "a dataflow step waited too long for its neighbourhood; results are invalid");
 }
 
-static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out) {
+// o: the kernels' observables, relative to the pressure reference p_ref in
+// effect when they were taken (the IOP and the mass carry it)
+static void fill_obs(const lbm_domain* d, const double* o, int64_t step, lbm_observables* out,
+                     double p_ref) {
     const lbm_params& p = d->params;
     const double scale = p.dt_s > 0.0 ? p.rho0 * (p.dx_m / p.dt_s) * (p.dx_m / p.dt_s) : 0.0;
     std::memset(out, 0, sizeof(*out));
     out->step = step;
-    out->iop = o[O_IOP];
-    out->iop_pa = p.p_sc_pa + scale * (o[O_IOP] - p.p_out);
+    out->iop = o[O_IOP] + p_ref;
+    out->iop_pa = p.p_sc_pa + scale * (out->iop - p.p_out);
     out->q_in = o[O_Q_IN];
     out->q_out = o[O_Q_OUT];
-    out->mass = o[O_MASS];
+    // sum_{i>=1} kappa_i = 4 sigma per active cell
+    out->mass = o[O_MASS] + 4.0 * K_SIGMA * p_ref * (double)d->info.n_active;
     out->peak_speed = o[O_PEAK];
     out->wss_cornea = o[O_WSS_C];
     out->wss_iris = o[O_WSS_I];
@@ -1134,7 +1220,7 @@ extern "C" lbm_status lbm_read_observables(lbm_domain* d, lbm_observables* out) 
     if (st != LBM_OK) return st;
     double o[NOBS];
     if ((st = fetch_obs(d, o)) != LBM_OK) return st;
-    fill_obs(d, o, d->step, out);
+    fill_obs(d, o, d->step, out, d->p_ref);
     return LBM_OK;
 }
 
@@ -1142,6 +1228,23 @@ extern "C" lbm_status lbm_read_observables(lbm_domain* d, lbm_observables* out) 
 // steps, the observing step, the fold of its partials and the read-back of
 // the observables and the dataflow status word into pinned slot `slot`.
 static constexpr int PIN_SLOT = NOBS + 1;  // doubles per slot (last: status word)
+
+// Re-centring of the pressure reference (FP32 and 16-bit storages): after a
+// steady-state check whose IOP lies more than PREF_TOL of it away from p_ref,
+// the stored populations move to p_ref = IOP.  One pass over them, enqueued
+// after whatever is already queued on the domain's stream (d->step, and so
+// the parity, already counts that work).
+static constexpr double PREF_TOL = 0.05;
+static lbm_status maybe_recenter(lbm_domain* d, double iop) {
+    if (d->prec == LBM_F64 || !std::isfinite(iop)) return LBM_OK;
+    if (std::fabs(iop - d->p_ref) <= PREF_TOL * std::fabs(iop)) return LBM_OK;
+    DISPATCH(d->prec, shift_pressure_kernel, d->d_desc, (int)(d->step & 1), iop - d->p_ref);
+    CK(cudaGetLastError());
+    d->p_ref = iop;
+    d->h.pd.p_out = d->params.p_out - d->p_ref;
+    d->h.pf.p_out = (float)d->h.pd.p_out;
+    return upload_desc(d);
+}
 
 static lbm_status enqueue_interval(lbm_domain* d, int32_t check_every, int slot) {
     lbm_status st;
@@ -1155,6 +1258,7 @@ static lbm_status enqueue_interval(lbm_domain* d, int32_t check_every, int slot)
     CK(cudaMemcpyAsync(reinterpret_cast<int*>(o + NOBS), d->d_flags, sizeof(int),
                        cudaMemcpyDeviceToHost, d->stream));
     CK(cudaEventRecord(d->pin_ev[slot], d->stream));
+    d->pin_pref[slot] = d->p_ref;
     if (!had_snap) {  // a snapshot exists from this observing step on
         d->h.snap_valid = 1;
         if ((st = upload_desc(d)) != LBM_OK) return st;
@@ -1215,9 +1319,9 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
                 drain();
                 return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)taken);
             }
-            fill_obs(d, o, s0 + taken - 1, &d->last_obs);
+            fill_obs(d, o, s0 + taken - 1, &d->last_obs, d->pin_pref[slot]);
             d->have_last_obs = true;
-            update_seepage(d, o[O_IOP]);
+            update_seepage(d, d->last_obs.iop);
             if (d->h.tm_model == 1) {
                 if ((st = upload_desc(d)) != LBM_OK) return st;
             }
@@ -1231,11 +1335,12 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
                     }
                     if (t[O_NAN] != 0.0)
                         return fail(LBM_EUNSTABLE, "NaN in the pressure field after %lld steps", (long long)queued);
-                    fill_obs(d, t, s0 + queued - 1, &d->last_obs);
-                    update_seepage(d, t[O_IOP]);
+                    fill_obs(d, t, s0 + queued - 1, &d->last_obs, d->pin_pref[next]);
+                    update_seepage(d, d->last_obs.iop);
                 }
                 return LBM_OK;
             }
+            if ((st = maybe_recenter(d, d->last_obs.iop)) != LBM_OK) { drain(); return st; }
             if (!ahead && more) {
                 had_snap[next] = d->h.snap_valid != 0;
                 if ((st = enqueue_interval(d, check_every, next)) != LBM_OK) return st;
@@ -1254,14 +1359,14 @@ extern "C" lbm_status lbm_run_to_steady(lbm_domain* d, double tol, int32_t check
 
 extern "C" lbm_status lbm_read_field(lbm_domain* d, double* u, double* p, double* T) {
     if (!d) return fail(LBM_EINVAL, "null domain");
-    DISPATCH(d->prec, fields_kernel, d->d_desc, (int)(d->step & 1), u, p, T);
+    DISPATCH(d->prec, fields_kernel, d->d_desc, (int)(d->step & 1), d->p_ref, u, p, T);
     CK(cudaGetLastError());
     return LBM_OK;
 }
 
 extern "C" lbm_status lbm_read_populations(lbm_domain* d, double* f, double* g) {
     if (!d) return fail(LBM_EINVAL, "null domain");
-    DISPATCH(d->prec, read_pops_kernel, d->d_desc, (int)(d->step & 1), f, g);
+    DISPATCH(d->prec, read_pops_kernel, d->d_desc, (int)(d->step & 1), d->p_ref, f, g);
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -1269,7 +1374,7 @@ extern "C" lbm_status lbm_read_populations(lbm_domain* d, double* f, double* g) 
 extern "C" lbm_status lbm_write_populations(lbm_domain* d, const double* f, const double* g) {
     if (!d) return fail(LBM_EINVAL, "null domain");
     if (!d->have_params) return fail(LBM_EINVAL, "parameters not set");
-    DISPATCH(d->prec, write_pops_kernel, d->d_desc, (int)(d->step & 1), f, g);
+    DISPATCH(d->prec, write_pops_kernel, d->d_desc, (int)(d->step & 1), d->p_ref, f, g);
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -1282,6 +1387,8 @@ struct StateHeader {
     double Tshift;
     double u_seep;
     lbm_params params;
+    double Tstep;  // 16-bit storages: step of the heat codes
+    double p_ref;  // pressure reference of the stored flow populations
 };
 }  // namespace
 
@@ -1296,7 +1403,7 @@ extern "C" lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes
     if (bytes < lbm_state_bytes(d)) return fail(LBM_ENOMEM, "state buffer too small");
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "LBMSTAT1", 8);
+    std::memcpy(hd.magic, "LBMSTAT2", 8);
     hd.nx = d->nx;
     hd.ny = d->ny;
     hd.prec = d->prec;
@@ -1304,6 +1411,8 @@ extern "C" lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes
     hd.step = d->step;
     hd.npad = d->L.npad;
     hd.Tshift = d->h.Tshift;
+    hd.Tstep = d->h.Tstep;
+    hd.p_ref = d->p_ref;
     hd.u_seep = d->u_seep;
     hd.params = d->params;
     std::memcpy(host_buf, &hd, sizeof(hd));
@@ -1318,14 +1427,18 @@ extern "C" lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t
     if (bytes < lbm_state_bytes(d)) return fail(LBM_ENOMEM, "state buffer too small");
     StateHeader hd;
     std::memcpy(&hd, host_buf, sizeof(hd));
-    if (std::memcmp(hd.magic, "LBMSTAT1", 8) != 0 || hd.nx != d->nx || hd.ny != d->ny ||
+    if (std::memcmp(hd.magic, "LBMSTAT2", 8) != 0 || hd.nx != d->nx || hd.ny != d->ny ||
         hd.prec != d->prec || hd.npad != d->L.npad)
         return fail(LBM_EINVAL, "checkpoint does not match this domain");
     d->u_seep = hd.u_seep;
+    d->p_ref = hd.p_ref;  // before apply_params, which sets the kernels' outlet pressure from it
     lbm_status st = apply_params(d, &hd.params);  // no reset: populations come from the buffer
     if (st != LBM_OK) return st;
     d->have_params = true;
-    d->h.Tshift = hd.Tshift;
+    d->h.Tshift = (float)hd.Tshift;
+    d->h.Tstep = (float)hd.Tstep;
+    d->h.Tscale = hd.Tstep > 0.0 ? (float)(1.0 / hd.Tstep) : 0.0f;
+    sync_heat_reference(d);
     d->h.snap_valid = 0;
     d->step = hd.step;
     if ((st = upload_desc(d)) != LBM_OK) return st;
@@ -1340,7 +1453,7 @@ extern "C" lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t
 
 extern "C" lbm_status lbm_set_launch(lbm_domain* d, const lbm_launch* l) {
     if (!d || !l) return fail(LBM_EINVAL, "null argument");
-    if (!launch_ok(*l)) return fail(LBM_EINVAL, "invalid launch shape");
+    if (!launch_ok(*l, d->prec)) return fail(LBM_EINVAL, "invalid launch shape");
     CK(cudaStreamSynchronize(d->stream));
     drop_graph(d);
     d->launch = *l;
@@ -1383,9 +1496,10 @@ namespace lbm {
 lbm_status set_error(lbm_status s, const char* msg) { return fail(s, "%s", msg); }
 
 bool domain_parts(const lbm_domain* d, const InstDesc** desc, int* precision, int* ny,
-                  int* parity, int* snap_valid, cudaStream_t* stream) {
+                  int* parity, int* snap_valid, cudaStream_t* stream, int* device) {
     if (!d) { fail(LBM_EINVAL, "null domain"); return false; }
     if (!d->have_params) { fail(LBM_EINVAL, "parameters not set"); return false; }
+    *device = d->device;
     *desc = d->d_desc;
     *precision = d->prec;
     *ny = d->ny;
@@ -1414,7 +1528,7 @@ bool domain_vortex_parts(const lbm_domain* d, const uint8_t** mask, int* nx, int
 }
 
 void fill_observables(const lbm_domain* d, const double* o, lbm_observables* out) {
-    fill_obs(d, o, d->step, out);
+    fill_obs(d, o, d->step, out, d->p_ref);
 }
 }  // namespace lbm
 
@@ -1477,7 +1591,7 @@ extern "C" lbm_status lbm_batch_create(int32_t precision, int32_t max_instances,
     if (!store_size(precision)) return fail(LBM_EINVAL, "unknown precision %d", precision);
     if (max_instances <= 0 || max_tiles <= 0 || max_tiles > INT32_MAX)
         return fail(LBM_EINVAL, "bad batch capacity");
-    if (launch && !launch_ok(*launch)) return fail(LBM_EINVAL, "invalid launch shape");
+    if (launch && !launch_ok(*launch, precision)) return fail(LBM_EINVAL, "invalid launch shape");
     const BatchLayout L = batch_layout(max_instances, max_tiles);
     if (!dev_buf || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_buf) % ALIGN) != 0)
         return fail(LBM_ENOMEM, "batch buffer too small or not 256-byte aligned (need %zu bytes)", L.total);
@@ -1689,15 +1803,17 @@ extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
     for (int k = 0; k < n; ++k) {
         lbm_domain* m = b->members[k];
         // the observing step ran at step - 1 (pre-collision state of that step)
-        fill_obs(m, b->hobs.data() + (size_t)k * NOBS, m->step - 1, &m->last_obs);
+        fill_obs(m, b->hobs.data() + (size_t)k * NOBS, m->step - 1, &m->last_obs, m->p_ref);
         m->have_last_obs = true;
         update_seepage(m, m->last_obs.iop);
         if (!m->h.snap_valid || m->h.tm_model == 1) {
             m->h.snap_valid = 1;
             if ((st = upload_desc(m)) != LBM_OK) return st;
         }
+        if ((st = maybe_recenter(m, m->last_obs.iop)) != LBM_OK) return st;
     }
-    return LBM_OK;
+    // the members' descriptors may have changed (snapshot, seepage, p_ref)
+    return batch_upload_table(b);
 }
 
 extern "C" lbm_status lbm_last_observables(const lbm_domain* d, lbm_observables* out) {
@@ -1715,7 +1831,7 @@ extern "C" lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_launch* l) {
 
 extern "C" lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_launch* l) {
     if (!b || !l) return fail(LBM_EINVAL, "null argument");
-    if (!launch_ok(*l)) return fail(LBM_EINVAL, "invalid launch shape");
+    if (!launch_ok(*l, b->prec)) return fail(LBM_EINVAL, "invalid launch shape");
     int64_t total = 0;
     for (lbm_domain* m : b->members) {
         lbm_status st = lbm_set_launch(m, l);
@@ -1754,7 +1870,10 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
         {64, 4, 1, 0, LBM_STEP_PER_LAUNCH},  {64, 4, 2, 0, LBM_STEP_PER_LAUNCH},
         {128, 1, 4, 0, LBM_STEP_PER_LAUNCH}, {128, 1, 8, 0, LBM_STEP_PER_LAUNCH},
         {256, 1, 8, 0, LBM_STEP_PER_LAUNCH}, {64, 4, 2, 0, LBM_STEP_FLOW},
-        {64, 4, 3, 0, LBM_STEP_FLOW},        {128, 2, 2, 0, LBM_STEP_FLOW}};
+        {64, 4, 3, 0, LBM_STEP_FLOW},        {128, 2, 2, 0, LBM_STEP_FLOW},
+        // 16-bit storages only: eight cells per thread on 256-cell rows
+        {256, 4, 1, 0, LBM_STEP_PER_LAUNCH}, {256, 4, 2, 0, LBM_STEP_PER_LAUNCH},
+        {256, 8, 1, 0, LBM_STEP_PER_LAUNCH}, {256, 4, 2, 0, LBM_STEP_FLOW}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1762,6 +1881,7 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
     lbm_launch best = b->launch;
     lbm_status st = LBM_OK;
     for (const lbm_launch& c : cand) {
+        if (!launch_ok(c, b->prec)) continue;  // a shape of another storage
         if ((st = lbm_batch_set_launch(b, &c)) != LBM_OK) {
             if (st == LBM_EBUSY) { st = LBM_OK; continue; }  // shape needs more tiles than fit
             break;

@@ -59,6 +59,10 @@ struct Phys {
     R drive_x, drive_y;
     R kwss;               // -(1 - 1/(2 tau))
     R u_seep;             // lumped TM: seepage speed out of the outlets
+    // Heat populations are stored (and, with FP32 arithmetic, collided) as
+    // deviations T_i - Tref/4 from a reference temperature fixed when the
+    // state is initialised (0 for FP64, T0 otherwise); dT0 = T0 - Tref.
+    R Tref, dT0;
 };
 
 // Everything a kernel needs to update one problem instance.  Lives in device
@@ -85,7 +89,8 @@ struct InstDesc {
     double arc_xc, arc_yc;
     Phys<double> pd;
     Phys<float> pf;
-    // 16-bit storage: stored = (value - shift) * scale
+    // 16-bit storage of the flow populations: stored = value * fscale.  Tshift
+    // = Tref / 4: every storage but FP64 holds T_i - Tshift
     float fscale, finv, Tshift, pad1;
     // bulk tensor copy map of the populations (staged kernel), or null; last,
     // so that adding it moved no field the other kernels read
@@ -93,6 +98,9 @@ struct InstDesc {
     // FOLD_MAX x NPART doubles of per-block partials for the observables'
     // fold, then its arrival counter (zero between folds)
     double* fold;
+    // 16-bit storages: heat deviations as 16-bit fixed point,
+    // code = round(value * Tscale), value = code * Tstep
+    float Tstep, Tscale;
 };
 // most blocks that fold one instance's tile partials
 constexpr int FOLD_MAX = 32;
@@ -117,8 +125,14 @@ struct Shape {
 };
 
 // Cells per thread along x: the FP32-arithmetic kernels take cell pairs
-// (vector loads and stores, warp shuffles), the FP64 kernel single cells.
-__host__ __device__ constexpr int cells_per_thread(int precision) { return precision == 0 ? 1 : 2; }
+// (vector loads and stores, warp shuffles), the FP64 kernel single cells, and
+// the 16-bit storages on 256-cell tile rows eight cells (one 16-byte vector
+// per plane).
+constexpr int VEC16_CELLS = 8;
+constexpr int VEC16_TILE_W = 32 * VEC16_CELLS;
+__host__ __device__ constexpr int cells_per_thread(int precision, int tile_w) {
+    return precision == 0 ? 1 : ((precision >= 2 && tile_w == VEC16_TILE_W) ? VEC16_CELLS : 2);
+}
 
 // ---- storage traits --------------------------------------------------------
 // Store cache policy of a storage trait.  ST_STREAM: evict-first streaming
@@ -132,6 +146,33 @@ __device__ __forceinline__ void st_pol(V* p, V v) {
     else __stcg(p, v);
 }
 
+// Heat deviations T_i - Tshift of the 16-bit storages: 16-bit fixed point,
+// companded.  The deviations of a run lie in a range known from its boundary
+// temperatures: near equilibrium |T_i - T0/4| <= span/4 (span: the largest
+// distance of a wall, inflow or reference temperature from T0), and the
+// steady state's heat depends on the rounding of these values through the
+// slowest diffusive modes, which amplify it by about 1/theta.  So the inner
+// three quarters of the codes (|code| <= TFIX_KNEE) carry that range with a
+// uniform step, several times finer than FP16's rounding at its ends.  While
+// a thermal boundary layer forms, anti-bounce-back at a wall of temperature
+// T_w returns deviations up to (T_w - T0)/2 - d*, up to 3/4 of span: the
+// outer codes cover them with a step TFIX_COARSE times coarser, out to about
+// span.  Codes saturate at +-32767.
+constexpr float TFIX_KNEE = 24576.0f;
+constexpr float TFIX_COARSE = 8.0f;
+__device__ __forceinline__ unsigned int enc_tfix(float v, const InstDesc& d) {
+    const float q = v * d.Tscale;
+    const float a = fabsf(q);
+    const float over = fmaxf(a - TFIX_KNEE, 0.0f);
+    const float c = fminf(rintf(a - over + over * (1.0f / TFIX_COARSE)), 32767.0f);
+    return (unsigned int)(unsigned short)(short)(int)copysignf(c, q);
+}
+__device__ __forceinline__ float dec_tfix(unsigned int h, const InstDesc& d) {
+    const float c = (float)(short)(unsigned short)h;
+    const float over = fmaxf(fabsf(c) - TFIX_KNEE, 0.0f);
+    return (c + copysignf(over * (TFIX_COARSE - 1.0f), c)) * d.Tstep;
+}
+
 // Populations are read through L2 only: each slot is read once per step, and
 // the dataflow kernel reads slots that other SMs wrote during the same launch.
 template <int POL = ST_STREAM>
@@ -139,6 +180,7 @@ struct StF64T {
     using T = double;
     using R = double;
     using A = double;  // per-thread and per-warp partials of the observables
+    static constexpr int kPol = POL;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
@@ -152,6 +194,7 @@ struct StF32T {
     using T = float;
     using R = float;
     using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
+    static constexpr int kPol = POL;
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc&) { return __ldcg(p); }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc&) { st_pol<POL>(p, v); }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc&) { return __ldcg(p); }
@@ -174,17 +217,22 @@ struct StF16T {
     using T = __half;
     using R = float;
     using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
+    static constexpr int kPol = POL;
+    // packed pairs of 16-bit codes (the vector path): the lower column in the
+    // low half of a 32-bit word
+    static __device__ __forceinline__ uint32_t encf2(float a, float b, const InstDesc& d) {
+        const __half2 h = __floats2half2_rn(a * d.fscale, b * d.fscale);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    static __device__ __forceinline__ float2 decf2(uint32_t w, const InstDesc& d) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        return make_float2(v.x * d.finv, v.y * d.finv);
+    }
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __half2float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
         st_pol<POL>(p, __float2half_rn(v * d.fscale));
-    }
-    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __half2float(__ldcg(p)) * d.finv + d.Tshift;
-    }
-    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        st_pol<POL>(p, __float2half_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
         const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
@@ -193,17 +241,28 @@ struct StF16T {
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
         st_pol<POL>(reinterpret_cast<__half2*>(p), __floats2half2_rn(a * d.fscale, b * d.fscale));
     }
+    static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) { return __half2float(*p) * d.finv; }
+    // heat deviations: 16-bit companded fixed point (enc_tfix / dec_tfix)
+    static __device__ __forceinline__ uint32_t encT2(float a, float b, const InstDesc& d) {
+        return enc_tfix(a, d) | (enc_tfix(b, d) << 16);
+    }
+    static __device__ __forceinline__ float2 decT2(uint32_t w, const InstDesc& d) {
+        return make_float2(dec_tfix(w & 0xFFFFu, d), dec_tfix(w >> 16, d));
+    }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
+        return dec_tfix(__ldcg(reinterpret_cast<const unsigned short*>(p)), d);
+    }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
+        st_pol<POL>(reinterpret_cast<unsigned short*>(p), (unsigned short)enc_tfix(v, d));
+    }
     static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
-        const float2 v = __half22float2(__ldcg(reinterpret_cast<const __half2*>(p)));
-        return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
+        return decT2(__ldcg(reinterpret_cast<const unsigned int*>(p)), d);
     }
     static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        st_pol<POL>(reinterpret_cast<__half2*>(p),
-               __floats2half2_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
+        st_pol<POL>(reinterpret_cast<unsigned int*>(p), encT2(a, b, d));
     }
-    static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) { return __half2float(*p) * d.finv; }
     static __device__ __forceinline__ R sldT(const T* p, const InstDesc& d) {
-        return __half2float(*p) * d.finv + d.Tshift;
+        return dec_tfix(*reinterpret_cast<const unsigned short*>(p), d);
     }
 };
 template <int POL = ST_STREAM>
@@ -211,17 +270,20 @@ struct StBF16T {
     using T = __nv_bfloat16;
     using R = float;
     using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
+    static constexpr int kPol = POL;
+    static __device__ __forceinline__ uint32_t encf2(float a, float b, const InstDesc& d) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a * d.fscale, b * d.fscale);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    static __device__ __forceinline__ float2 decf2(uint32_t w, const InstDesc& d) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+        return make_float2(v.x * d.finv, v.y * d.finv);
+    }
     static __device__ __forceinline__ R ldf(const T* p, const InstDesc& d) {
         return __bfloat162float(__ldcg(p)) * d.finv;
     }
     static __device__ __forceinline__ void stf(T* p, R v, const InstDesc& d) {
         st_pol<POL>(p, __float2bfloat16_rn(v * d.fscale));
-    }
-    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
-        return __bfloat162float(__ldcg(p)) * d.finv + d.Tshift;
-    }
-    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
-        st_pol<POL>(p, __float2bfloat16_rn((v - d.Tshift) * d.fscale));
     }
     static __device__ __forceinline__ float2 ldf2(const T* p, const InstDesc& d) {
         const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
@@ -230,19 +292,30 @@ struct StBF16T {
     static __device__ __forceinline__ void stf2(T* p, float a, float b, const InstDesc& d) {
         st_pol<POL>(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a * d.fscale, b * d.fscale));
     }
-    static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
-        const float2 v = __bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p)));
-        return make_float2(v.x * d.finv + d.Tshift, v.y * d.finv + d.Tshift);
-    }
-    static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
-        st_pol<POL>(reinterpret_cast<__nv_bfloat162*>(p),
-               __floats2bfloat162_rn((a - d.Tshift) * d.fscale, (b - d.Tshift) * d.fscale));
-    }
     static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) {
         return __bfloat162float(*p) * d.finv;
     }
+    // heat deviations: 16-bit companded fixed point (enc_tfix / dec_tfix)
+    static __device__ __forceinline__ uint32_t encT2(float a, float b, const InstDesc& d) {
+        return enc_tfix(a, d) | (enc_tfix(b, d) << 16);
+    }
+    static __device__ __forceinline__ float2 decT2(uint32_t w, const InstDesc& d) {
+        return make_float2(dec_tfix(w & 0xFFFFu, d), dec_tfix(w >> 16, d));
+    }
+    static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
+        return dec_tfix(__ldcg(reinterpret_cast<const unsigned short*>(p)), d);
+    }
+    static __device__ __forceinline__ void stT(T* p, R v, const InstDesc& d) {
+        st_pol<POL>(reinterpret_cast<unsigned short*>(p), (unsigned short)enc_tfix(v, d));
+    }
+    static __device__ __forceinline__ float2 ldT2(const T* p, const InstDesc& d) {
+        return decT2(__ldcg(reinterpret_cast<const unsigned int*>(p)), d);
+    }
+    static __device__ __forceinline__ void stT2(T* p, float a, float b, const InstDesc& d) {
+        st_pol<POL>(reinterpret_cast<unsigned int*>(p), encT2(a, b, d));
+    }
     static __device__ __forceinline__ R sldT(const T* p, const InstDesc& d) {
-        return __bfloat162float(*p) * d.finv + d.Tshift;
+        return dec_tfix(*reinterpret_cast<const unsigned short*>(p), d);
     }
 };
 

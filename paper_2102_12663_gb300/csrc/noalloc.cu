@@ -27,7 +27,7 @@ namespace lbm {
 // internal accessors of lbm_api.cu
 lbm_status set_error(lbm_status s, const char* msg);
 bool domain_parts(const lbm_domain* d, const InstDesc** desc, int* precision, int* ny,
-                  int* parity, int* snap_valid, cudaStream_t* stream);
+                  int* parity, int* snap_valid, cudaStream_t* stream, int* device);
 void fill_observables(const lbm_domain* d, const double* o, lbm_observables* out);
 
 // One NPART-double partial per grid row, then the NOBS finalised values.
@@ -132,10 +132,22 @@ static lbm_status cuda_fail(const char* what, cudaError_t e) {
 
 extern "C" lbm_status lbm_read_observables_noalloc(lbm_domain* dom, lbm_observables* out) {
     const InstDesc* desc = nullptr;
-    int prec = 0, ny = 0, parity = 0, snap_valid = 0;
+    int prec = 0, ny = 0, parity = 0, snap_valid = 0, device = 0, current = 0;
     cudaStream_t s = nullptr;
     if (!out) return set_error(LBM_EINVAL, "null output");
-    if (!domain_parts(dom, &desc, &prec, &ny, &parity, &snap_valid, &s)) return LBM_EINVAL;
+    if (!domain_parts(dom, &desc, &prec, &ny, &parity, &snap_valid, &s, &device)) return LBM_EINVAL;
+    // the scratch address below is the current device's: it must be the
+    // domain's (a device switch since lbm_create_domain would hand the kernels
+    // another device's address)
+    cudaError_t e = cudaGetDevice(&current);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    if (current != device) {
+        char buf[160];
+        snprintf(buf, sizeof(buf),
+                 "the current device is %d but the domain was created on device %d; make it "
+                 "current before lbm_read_observables_noalloc", current, device);
+        return set_error(LBM_EINVAL, buf);
+    }
     if (ny > LBM_NOALLOC_MAX_ROWS) {
         char buf[160];
         snprintf(buf, sizeof(buf),
@@ -144,7 +156,7 @@ extern "C" lbm_status lbm_read_observables_noalloc(lbm_domain* dom, lbm_observab
         return set_error(LBM_EINVAL, buf);
     }
     double* scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress of the scratch array", e);
     const int mode = OBS_STATS | (snap_valid ? OBS_RESID : 0);
     switch (prec) {

@@ -9,6 +9,12 @@
 
 namespace lbm {
 
+// precision code of a storage trait (1 f32, 2 f16-dev, 3 bf16-dev)
+template <class ST>
+static constexpr int storage_precision() {
+    return sizeof(typename ST::T) == 4 ? 1 : (std::is_same<typename ST::T, __half>::value ? 2 : 3);
+}
+
 template <class ST>
 static StepPlan plan_t(int mode, Shape shape) {
     const bool obs = mode != 0;
@@ -39,7 +45,7 @@ static StepPlan plan_t(int mode, Shape shape) {
         p.func = !obs ? reinterpret_cast<const void*>(&step_kernel<ST, false>)
                  : (mode & OBS_WRITE) ? reinterpret_cast<const void*>(&step_kernel<ST, true, typename ST::A>)
                                       : reinterpret_cast<const void*>(&step_kernel<ST, true>);
-        p.block = dim3(shape.tw / cells_per_thread(1), shape.bh);
+        p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
         p.smem = 0;
     }
     return p;
@@ -57,7 +63,7 @@ template <class ST>
 static StepPlan flow_t(Shape shape) {
     StepPlan p;
     p.func = reinterpret_cast<const void*>(&step_kernel_flow<ST>);
-    p.block = dim3(shape.tw / cells_per_thread(1), shape.bh);
+    p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
     p.smem = 0;
     return p;
 }

@@ -15,6 +15,10 @@ shared launches.
 ``solve_one_at_a_time`` is the plain baseline: every request on its own FP32
 domain, one after the other, through lbm_run_to_steady.
 
+A request may carry its own steady tolerance (the 16-bit storages settle on
+a residual noise floor above the FP32 criterion) and its own step cap
+(workloads.steady_step_cap: a number of decay times of its slowest mode).
+
 This module only orchestrates; every step of every solve runs in the CUDA
 library.
 """
@@ -36,6 +40,8 @@ class Request:
     params: dict
     precision: str = "f32"
     arrival_s: float = 0.0
+    tol: float | None = None      # steady tolerance (None: the server's)
+    max_steps: int | None = None  # step cap (None: the server's)
 
 
 @dataclasses.dataclass
@@ -57,13 +63,22 @@ class Result:
         return self.finish_s - self.arrival_s
 
 
-def requests_from_draws(draws) -> list:
-    """Requests from workloads.request_stream / batch_instances draws."""
+def requests_from_draws(draws, tol_by_precision: dict | None = None, cap_efolds: float | None = None,
+                        check_every: int = 100) -> list:
+    """Requests from workloads.request_stream / batch_instances draws.
+    tol_by_precision (e.g. workloads.SERVE_TOL) sets each request's steady
+    tolerance by its storage; cap_efolds sets its step cap to that many decay
+    times of its slowest viscous mode (workloads.steady_step_cap)."""
+    from . import workloads as W
     out = []
     for d in draws:
+        prec = "f16" if d.get("fp16") else "f32"
+        nu = (2.0 * d["params"]["tau"] - 1.0) / 6.0
         out.append(Request(id=d["id"], nx=d["nx"], ny=d["ny"], angle_deg=d["angle_deg"],
-                           params=d["params"], precision="f16" if d.get("fp16") else "f32",
-                           arrival_s=d.get("arrival_s", 0.0)))
+                           params=d["params"], precision=prec, arrival_s=d.get("arrival_s", 0.0),
+                           tol=(tol_by_precision or {}).get(prec),
+                           max_steps=(W.steady_step_cap(d["ny"], nu, cap_efolds, check_every)
+                                      if cap_efolds else None)))
     return out
 
 
@@ -135,9 +150,11 @@ class Server:
         for rid in list(self.active):
             req, dom, nbytes, t_admit = self.active[rid]
             o = dom.last_observables()
-            converged = 0.0 <= o["residual"] < self.tol
+            tol = self.tol if req.tol is None else req.tol
+            cap = self.max_steps if req.max_steps is None else req.max_steps
+            converged = 0.0 <= o["residual"] < tol
             unstable = bool(o["nan_flag"])
-            if converged or unstable or dom.step_count >= self.max_steps:
+            if converged or unstable or dom.step_count >= cap:
                 b = self.batches[req.precision]
                 b.remove(dom)
                 self.results.append(Result(req.id, req.precision, req.nx, req.ny, dom.step_count,
@@ -198,7 +215,8 @@ def solve_one_at_a_time(requests, tol: float = 1e-7, check_every: int = 100,
             dom.set_launch(**launch)
             dom.set_params(r.params)
             try:
-                st, steps = dom.run_to_steady(tol, check_every=check_every, max_steps=max_steps)
+                st, steps = dom.run_to_steady(tol if r.tol is None else r.tol, check_every=check_every,
+                                              max_steps=max_steps if r.max_steps is None else r.max_steps)
                 unstable = False
             except lbm.LBMError as e:
                 if e.status != lbm.EUNSTABLE:

@@ -152,3 +152,19 @@ def request_stream(n: int, rate_hz: float = 20.0, seed: int = 2102, ny_lo: int =
         t += rng.exponential(1.0 / rate_hz)
         r["arrival_s"] = t
     return inst
+
+
+# Steady-state tolerance of served solves per storage: max |du| over a
+# 100-step check interval.  FP32 and FP64 reach the 1e-7 criterion; the 16-bit
+# storages re-round every population each step, and their residual settles on
+# a noise floor (about 3e-6 per 100 steps for FP16, 4e-5 for BF16 on the
+# 256 x 128 eye), so they take the lowest tolerance above it.
+SERVE_TOL = {"f64": 1e-7, "f32": 1e-7, "f16": 1e-5, "bf16": 1e-4}
+
+
+def steady_step_cap(ny: int, nu: float, efolds: float = 20.0, check_every: int = 100) -> int:
+    """Step cap of a steady solve: `efolds` decay times 1/(nu k^2) of the
+    slowest viscous mode across the chamber (k = pi / ny), rounded up to whole
+    check intervals."""
+    steps = efolds * ny * ny / (math.pi ** 2 * nu)
+    return int(math.ceil(steps / check_every) * check_every)

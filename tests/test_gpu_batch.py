@@ -93,6 +93,16 @@ def test_batch_matches_oracle_with_mixed_parity():
     assert o["iop"] == pytest.approx(oo["iop"], rel=1e-12)
     assert o["wss_cornea"] == pytest.approx(oo["wss_cornea"], rel=1e-12)
     assert o["mass"] == pytest.approx(oo["mass"], rel=1e-12)
+    # a second check: its residual against the first check's velocity (S9)
+    snap = r0.fields()[0].copy()
+    b.check(20)
+    r0.run(20)
+    oo = r0.observe(snap)
+    o = doms[0].last_observables()
+    assert o["step"] == 84 and oo["residual"] > 0.0
+    assert o["residual"] == pytest.approx(oo["residual"], rel=1e-12)
+    for r in refs:
+        r.run(20)
     # removal hands the domain back; it keeps stepping alone
     b.remove(doms[2])
     doms[2].step(5)

@@ -232,6 +232,36 @@ def test_run_to_steady_and_errors():
         dom.set_params(dict(P, g_beta=1e-3, g_dir=(1.0, 1.0)))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_steady_check_residual_matches_oracle(prec):
+    """S9, the steady-state check: the residual of a check is the maximum over
+    active cells of |u(n) - u(n - 100)|, u of Eq. 9, against the oracle's
+    residual with the velocity of the previous check as its snapshot.  Each
+    check observes the last step of its interval, so the second check of a
+    run from step s0 compares the states after s0 + 199 and s0 + 99 steps.
+    FP32: u sums six populations, so each velocity is off by at most 6 times
+    the population tolerance, and the residual by twice that."""
+    dom, ref, pp = eye_pair(160, 80, prec)
+    s0 = 300
+    dom.step(s0)
+    st, steps = dom.run_to_steady(0.0, check_every=100, max_steps=200)
+    assert st == lbm.ENOTCONVERGED and steps == 200
+    o = dom.last_observables()
+    assert o["step"] == s0 + 199
+    ref.run(s0 + 99)
+    snap = ref.fields()[0].copy()
+    ref.run(100)
+    oo = ref.observe(snap)
+    assert oo["residual"] > 1e-7  # the flow is still developing
+    if prec == "f64":
+        assert o["residual"] == pytest.approx(oo["residual"], rel=1e-12)
+        assert o["iop"] == pytest.approx(oo["iop"], rel=1e-12)
+        assert o["peak_speed"] == pytest.approx(oo["peak"], rel=1e-12)
+    else:
+        bound = 12 * tol("f32", s0 + 200) * np.abs(ref.f).max()
+        assert abs(o["residual"] - oo["residual"]) <= bound
+
+
 def test_unstable_parameters_report_nan():
     """A deliberately unstable run (huge inflow at tau close to 1/2) is caught
     by the NaN flag and reported as EUNSTABLE, not as a fault."""
@@ -427,3 +457,51 @@ def test_fp32_observables_any_block_width(launch):
                   ("wss_cornea", "wss_cornea"), ("wss_iris", "wss_iris")]:
         assert o[k] == pytest.approx(oo[kr], rel=2e-5), k
     assert o["residual"] > 0.0
+
+
+VEC16_SHAPES = [
+    dict(tile_w=256, block_rows=2, rows_per_thread=2, blocks_per_sm=0, stepping=lbm.STEP_PER_LAUNCH),
+    dict(tile_w=256, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=lbm.STEP_FLOW),
+]
+
+
+@pytest.mark.parametrize("prec,unit_roundoff", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("nx,ny", [(512, 256), (520, 130), (516, 130)])
+@pytest.mark.parametrize("launch", range(len(VEC16_SHAPES)))
+def test_vector16_path_eye(prec, unit_roundoff, nx, ny, launch):
+    """The eight-cell vector path of the 16-bit storages (256-cell tile rows,
+    one 16-byte vector per plane and lane) against the FP64 oracle after an
+    odd and an even number of steps (a few unit roundoffs times sqrt(n), as
+    for the pair path), and against the pair-path shape within the same
+    bound.  512 x 256 has whole interior rows; 520 x 130 ends in a partial
+    tile (the last segment falls back to cell pairs); 516 x 130 is no multiple
+    of eight columns (every row falls back)."""
+    dom, ref, _ = eye_pair(nx, ny, prec, launch=VEC16_SHAPES[launch])
+    pair, _, _ = eye_pair(nx, ny, prec, launch=dict(tile_w=64, block_rows=4, rows_per_thread=1))
+    done = 0
+    for n in (1, 40):
+        dom.step(n)
+        pair.step(n)
+        ref.run(n)
+        done += n
+        bound = 4.0 * unit_roundoff * done ** 0.5
+        assert rel_err(dom, ref) <= bound, done
+        fv, gv = pops(dom)
+        fp, gp = pops(pair)
+        assert np.abs(fv - fp).max() <= bound * np.abs(ref.f).max()
+        assert np.abs(gv - gp).max() <= bound * np.abs(ref.T).max()
+
+
+@pytest.mark.parametrize("prec,unit_roundoff", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_vector16_path_periodic_wrap(prec, unit_roundoff):
+    """Vector rows that wrap around periodic edges: the lanes at column 0 and
+    at the last column fetch and store the code across the edge."""
+    m, d = W.porous_box(256, 24)
+    m[5:9, 20:60] = 1
+    m[12:14, :] = 0
+    P = dict(tau=0.7, tau_T=0.8, drive=(1e-5, -3e-6), K_tm=0.2, noise_amp=1e-3, T0=0.3,
+             g_beta=1e-4, g_dir=(0.6, -0.8), seed=9)
+    dom, ref = mask_pair(m, d, prec, P, launch=VEC16_SHAPES[0])
+    dom.step(61)
+    ref.run(61)
+    assert rel_err(dom, ref) <= 4.0 * unit_roundoff * 61 ** 0.5

@@ -38,7 +38,7 @@ def _same(a, b):
         assert a[k] == pytest.approx(b[k], rel=REL, abs=1e-300), k
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 def test_noalloc_matches_read_observables_twice(prec):
     L = lbm.load(build_if_missing=True)
     dom = lbm.Domain(dict(nx=160, ny=80, angle_deg=45.0), precision=prec)
@@ -68,3 +68,23 @@ def test_noalloc_rejects_grids_taller_than_its_scratch():
     assert rc == lbm.EINVAL
     assert b"8192" in L.lbm_last_error()
     dom.close()
+
+
+def test_noalloc_reads_a_batch_member():
+    """A member of a batch: its work runs on the batch's stream, so the read
+    follows the batch's steps and matches lbm_read_observables of the member."""
+    L = lbm.load(build_if_missing=True)
+    doms = []
+    for ny in (64, 80):
+        d = lbm.Domain(dict(nx=2 * ny, ny=ny, angle_deg=40.0), precision="f64")
+        d.set_params(W.eye_params(ny, tau=0.8, Ra=1e4, K_tm=0.05))
+        doms.append(d)
+    b = lbm.Batch("f64", max_instances=2, max_tiles=1 << 14)
+    for d in doms:
+        b.add(d)
+    b.step(37)
+    b.check(20)
+    b.step(5)
+    for d in doms:
+        _same(_noalloc(L, d), d.observables())
+    b.close()
