@@ -435,8 +435,10 @@ LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepp
               sweep_lag=0)
 # the studies (other grid sizes and many small grids): one launch per step
 STUDY_LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
-# 16-bit storages: 256-cell tile rows, eight cells per thread
-VEC16_LAUNCH = dict(tile_w=256, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=0)
+# 16-bit storages: 128-cell tile rows, four cells per thread (8-byte vectors);
+# measured ahead of the eight-cell rows (133.7 against 136.4 us per step of
+# the 8192 x 4096 eye) and of cell pairs (142.4 us)
+VEC16_LAUNCH = dict(tile_w=128, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):
@@ -627,38 +629,93 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Poisson stream (mean 20/s) of steady-solve requests, NY log-uniform
-    128..2048, FP32 or FP16 storage with p = 1/2, 150 GB HBM budget; steady
-    criterion max |du| < 1e-7 per 100 steps with a step cap."""
+    """Poisson stream (mean 20/s) of steady-solve requests: NY log-uniform over
+    [--serve-ny-lo, --serve-ny-hi] (default 64..256, NX = 2 NY), parameters
+    drawn as in the batching workload, FP32 or FP16 storage with p = 1/2, 150 GB
+    HBM budget.  Each request runs until its residual over a 100-step check
+    falls below 1e-7 or it reaches a cap of 20 decay times of its slowest
+    viscous mode; an FP16 request runs in FP16 until 1e-5 (its storage's noise
+    floor lies above 1e-7) and then in FP32.
+    The baseline solves every request alone on a plain FP32 domain at the FP32
+    tolerance, one after the other.  A seeded sample of the served results, and
+    the baseline's results for the same requests, are compared with FP64 solves
+    of those requests (to 1e-9 per 100 steps)."""
+    import numpy as np
     import torch
 
     from paper_2102_12663_gb300 import lbm, serve
     from paper_2102_12663_gb300 import workloads as W
     torch.cuda.set_device(0)
     lbm.load(build_if_missing=True)
-    draws = W.request_stream(args.requests, rate_hz=20.0, ny_lo=128, ny_hi=2048, fp16_share=0.5)
-    reqs = serve.requests_from_draws(draws)
-    srv = serve.Server(budget_bytes=150e9, tol=1e-7, check_every=CHECK, max_steps=args.cap,
-                       launch=STUDY_LAUNCH)
+    draws = W.request_stream(args.requests, rate_hz=20.0, ny_lo=args.serve_ny_lo, ny_hi=args.serve_ny_hi,
+                             fp16_share=0.5)
+    reqs = serve.requests_from_draws(draws, tol_by_precision=W.SERVE_TOL, cap_efolds=20.0)
+    refine = {"f16": W.SERVE_TOL["f32"]}
+    srv = serve.Server(budget_bytes=150e9, tol=1e-7, check_every=CHECK, max_steps=10**9,
+                       launch=STUDY_LAUNCH, refine_tol=refine)
     res = srv.run(reqs, realtime=True)
     s_served = serve.summary(res, srv.wall_s)
     s_served["peak_hbm_bytes"] = srv.peak_used
     s_served["cell_updates_per_s"] = srv.cell_updates / srv.wall_s
+    f16 = [r for r in res if r.precision == "f16"]
+    s_served["f16_steps_share_in_f16"] = (sum(r.steps - r.refined_steps for r in f16)
+                                          / max(1, sum(r.steps for r in f16)))
     srv.close()
-    base = serve.solve_one_at_a_time(serve.requests_from_draws(draws), tol=1e-7, check_every=CHECK,
-                                     max_steps=args.cap, launch=STUDY_LAUNCH, realtime=True)
+    base_reqs = serve.requests_from_draws(draws, tol_by_precision={"f32": W.SERVE_TOL["f32"],
+                                                                   "f16": W.SERVE_TOL["f32"]},
+                                          cap_efolds=20.0)
+    base = serve.solve_one_at_a_time(base_reqs, check_every=CHECK, launch=STUDY_LAUNCH, realtime=True)
     wall = max(r.finish_s for r in base)
     s_base = serve.summary(base, wall)
+
+    # accuracy: FP64 solves of a seeded sample of requests of each storage
+    keys = ("iop", "peak_speed", "wss_cornea", "wss_iris")
+    rng = np.random.Generator(np.random.PCG64(2102))
+    by_id = {r.id: r for r in res}
+    base_by_id = {r.id: r for r in base}
+    acc = {}
+    for prec in ("f16", "f32"):
+        ids = sorted(r.id for r in res if r.precision == prec and r.converged)
+        pick = sorted(rng.choice(ids, size=min(args.accuracy_sample, len(ids)), replace=False).tolist()) if ids else []
+        errs, same, base_errs = ({k: [] for k in keys} for _ in range(3))
+        for rid in pick:
+            q = next(r for r in reqs if r.id == rid)
+            nu = (2.0 * q.params["tau"] - 1.0) / 6.0
+            refs = []
+            # FP64 converged (1e-9 per 100 steps), and FP64 under the request's own stopping rule
+            for tol in (1e-9, refine.get(q.precision, q.tol)):
+                dom = lbm.Domain(dict(nx=q.nx, ny=q.ny, angle_deg=q.angle_deg), precision="f64")
+                dom.set_launch(**STUDY_LAUNCH)
+                dom.set_params(q.params)
+                dom.run_to_steady(tol, check_every=CHECK, max_steps=W.steady_step_cap(q.ny, nu, 40.0))
+                refs.append(dom.last_observables())
+                dom.close()
+            conv, rule = refs
+            for k in keys:
+                errs[k].append(abs(by_id[rid].observables[k] - conv[k]) / abs(conv[k]))
+                same[k].append(abs(by_id[rid].observables[k] - rule[k]) / abs(rule[k]))
+                base_errs[k].append(abs(base_by_id[rid].observables[k] - conv[k]) / abs(conv[k]))
+        mx = lambda d: {k: max(v) if v else None for k, v in d.items()}
+        acc[prec] = {"requests": pick, "tolerance": refine.get(prec, W.SERVE_TOL[prec]),
+                     "served_max_rel_err_vs_fp64_converged": mx(errs),
+                     "served_median_rel_err_vs_fp64_converged":
+                         {k: float(np.median(v)) if v else None for k, v in errs.items()},
+                     "served_max_rel_err_vs_fp64_same_rule": mx(same),
+                     "baseline_fp32_max_rel_err_vs_fp64_converged": mx(base_errs)}
     line = {"metric": "served steady solves per second", "value": s_served["solves_per_s"],
             "unit": "solves/s", "higher_is_better": True, "dtype": "f32+f16 storage",
             "data": "synthetic",
             "config": {"workload": f"{args.requests} Poisson requests (mean 20/s), NY log-uniform "
-                                   f"128..2048, FP16 storage p=1/2, budget 150 GB, tol 1e-7 per 100 "
-                                   f"steps, cap {args.cap} steps"},
+                                   f"{args.serve_ny_lo}..{args.serve_ny_hi} (NX = 2 NY), FP16 storage p=1/2, "
+                                   f"budget 150 GB; steady at max|du| per 100 steps < 1e-7; FP16 requests "
+                                   f"run in FP16 to 1e-5, then in FP32 to 1e-7; cap 20 viscous decay times "
+                                   f"of the request",
+                       "tolerances": W.SERVE_TOL, "refine": refine},
             "served": s_served, "one_at_a_time_fp32": s_base,
             "speedup_solves_per_s": s_served["solves_per_s"] / s_base["solves_per_s"],
             "p50_ratio": s_base["p50_s"] / s_served["p50_s"],
-            "p99_ratio": s_base["p99_s"] / s_served["p99_s"]}
+            "p99_ratio": s_base["p99_s"] / s_served["p99_s"],
+            "accuracy_vs_fp64": acc}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -691,7 +748,10 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=500, help="oracle cross-check steps")
     ap.add_argument("--steady-grid", default="256x128", help="grid of the steady-state error study")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
-    ap.add_argument("--cap", type=int, default=10000, help="serving: step cap per request")
+    ap.add_argument("--serve-ny-lo", type=int, default=64, help="serving: smallest NY of a request")
+    ap.add_argument("--serve-ny-hi", type=int, default=256, help="serving: largest NY of a request")
+    ap.add_argument("--accuracy-sample", type=int, default=4,
+                    help="serving: requests per storage solved again in FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

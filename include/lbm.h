@@ -420,9 +420,12 @@ lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_launch* launch);
 lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_launch* launch);
 
 /* Autotuner: time a fixed set of candidate shapes (tile width, rows per
- * thread, persistent grids) for steps_per_candidate steps each on the current
- * members, keep the fastest and report it in *chosen (may be NULL).  The timed
- * steps are real steps of the members. */
+ * thread, persistent grids, stepping; the 16-bit storages add eight-cell
+ * shapes) for steps_per_candidate steps each on the current members, keep the
+ * fastest and report it in *chosen (may be NULL).  One-launch-per-step shapes
+ * are timed twice: with the merged tile list in member order, and with the
+ * tiles that hold boundary cells first; the faster order is kept with the
+ * shape.  The timed steps are real steps of the members. */
 lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, lbm_launch* chosen);
 
 /* Algorithmic bytes of one batch step (sum of lbm_step_bytes of the members)

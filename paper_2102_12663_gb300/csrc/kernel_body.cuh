@@ -901,10 +901,31 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
 // lo and whose high half is the low half of hi (a one-code shift)
 __device__ __forceinline__ uint32_t shift_pair(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x5432); }
 
-template <class ST, int PAR>
+// NW packed 32-bit words (2 NW cells) per plane and lane: one 16-byte (NW = 4)
+// or 8-byte (NW = 2) vector access
+template <int NW>
+__device__ __forceinline__ void ld_words(const void* p, uint32_t* w) {
+    if constexpr (NW == 4) {
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else {
+        const uint2 v = __ldcg(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    }
+}
+template <int POL, int NW>
+__device__ __forceinline__ void st_words(void* p, const uint32_t* w) {
+    if constexpr (NW == 4) st_pol<POL>(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+    else st_pol<POL>(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+}
+
+template <class ST, int PAR, int NW>
 __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0, int y, uint32_t por) {
     using T = typename ST::T;
     static_assert(sizeof(T) == 2, "16-bit storages only");
+    static_assert(NW == 2 || NW == 4, "8-byte or 16-byte vectors");
+    constexpr int POL = ST::kPol;
+    constexpr int C = 2 * NW;  // cells per lane
     const int nx = d.nx, ny = d.ny;
     const int np = (int)d.npad;
     T* const P = static_cast<T*>(d.pops);
@@ -912,39 +933,38 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
     const int row = y * nx;
     const int rowu = (y == ny - 1 ? 0 : y + 1) * nx;
     const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
-    const int xl = x0 == 0 ? nx - 1 : x0 - 1;          // column left of the lane's cells
-    const int xr = x0 + VEC16_CELLS == nx ? 0 : x0 + VEC16_CELLS;  // column right of them
-    uint32_t w[13][4];
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;  // column left of the lane's cells
+    const int xr = x0 + C == nx ? 0 : x0 + C;  // column right of them
+    uint32_t w[13][NW];
 
     // ---- load -------------------------------------------------------------
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
         if (PAR == 0 || k == 0) {
-            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(P + k * np + row + x0));
-            w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+            ld_words<NW>(P + k * np + row + x0, w[k]);
         } else {
             const bool heat = k > 8;
             const int i = heat ? k - 8 : k;             // lattice direction
             const int pl = heat ? 8 + opp(i) : opp(i);  // f_i(x) sits in slot (x - e_i, opp(i))
             const int sr = ey(i) == 1 ? rowd : (ey(i) == -1 ? rowu : row);
             const T* src = P + pl * np + sr;
-            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(src + x0));
+            uint32_t v[NW];
+            ld_words<NW>(src + x0, v);
             if (ex(i) == 0) {
-                w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
-            } else if (ex(i) == 1) {  // source columns x0 - 1 .. x0 + 6
-                uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+#pragma unroll
+                for (int j = 0; j < NW; ++j) w[k][j] = v[j];
+            } else if (ex(i) == 1) {  // source columns x0 - 1 .. x0 + C - 2
+                uint32_t prev = __shfl_up_sync(0xffffffffu, v[NW - 1], 1);
                 if (lane == 0) prev = (uint32_t)__ldcg(reinterpret_cast<const unsigned short*>(src + xl)) << 16;
-                w[k][0] = shift_pair(prev, v.x);
-                w[k][1] = shift_pair(v.x, v.y);
-                w[k][2] = shift_pair(v.y, v.z);
-                w[k][3] = shift_pair(v.z, v.w);
-            } else {                  // source columns x0 + 1 .. x0 + 8
-                uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+                w[k][0] = shift_pair(prev, v[0]);
+#pragma unroll
+                for (int j = 1; j < NW; ++j) w[k][j] = shift_pair(v[j - 1], v[j]);
+            } else {                  // source columns x0 + 1 .. x0 + C
+                uint32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
                 if (lane == 31) next = (uint32_t)__ldcg(reinterpret_cast<const unsigned short*>(src + xr));
-                w[k][0] = shift_pair(v.x, v.y);
-                w[k][1] = shift_pair(v.y, v.z);
-                w[k][2] = shift_pair(v.z, v.w);
-                w[k][3] = shift_pair(v.w, next);
+#pragma unroll
+                for (int j = 0; j < NW - 1; ++j) w[k][j] = shift_pair(v[j], v[j + 1]);
+                w[k][NW - 1] = shift_pair(v[NW - 1], next);
             }
         }
     }
@@ -954,13 +974,12 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
     // step: assembled from plane opp(k)); the result of direction k goes to
     // plane opp(k) of the cells' own columns on an even step and to plane k,
     // shifted by e_k, on an odd step.  Each pass takes word 0 of every plane
-    // (cells 2q and 2q + 1) and moves the result word to the back, so after
-    // four passes every plane's words are the results in their own places.
-    // The pass is not unrolled: every register index stays static, and the
-    // loop body (two inlined collisions) stays small enough for the
-    // instruction cache.
+    // (two cells) and moves the result word to the back, so after NW passes
+    // every plane's words are the results in their own places.  The pass loop
+    // is not unrolled: every register index stays static, and the body (two
+    // inlined collisions) stays small enough for the instruction cache.
 #pragma unroll 1
-    for (int q = 0; q < VEC16_CELLS / 2; ++q) {
+    for (int q = 0; q < NW; ++q) {
         float a[13], b[13];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -984,10 +1003,9 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
         }
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
-            w[k][0] = w[k][1];
-            w[k][1] = w[k][2];
-            w[k][2] = w[k][3];
-            w[k][3] = o[k];
+#pragma unroll
+            for (int j = 0; j < NW - 1; ++j) w[k][j] = w[k][j + 1];
+            w[k][NW - 1] = o[k];
         }
     }
 
@@ -995,7 +1013,7 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
         if (PAR == 0 || k == 0) {
-            st_pol<ST::kPol>(reinterpret_cast<uint4*>(P + k * np + row + x0), make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]));
+            st_words<POL, NW>(P + k * np + row + x0, w[k]);
             continue;
         }
         const bool heat = k > 8;
@@ -1003,33 +1021,42 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
         const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);  // f*_i(x) goes to slot (x + e_i, i)
         T* const dst = P + k * np + dr;
         if (ex(i) == 0) {
-            st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]));
-        } else if (ex(i) == 1) {  // destination columns x0 + 1 .. x0 + 8
-            const uint32_t prev = __shfl_up_sync(0xffffffffu, w[k][3], 1);
-            const uint4 o = make_uint4(shift_pair(prev, w[k][0]), shift_pair(w[k][0], w[k][1]),
-                                       shift_pair(w[k][1], w[k][2]), shift_pair(w[k][2], w[k][3]));
+            st_words<POL, NW>(dst + x0, w[k]);
+        } else if (ex(i) == 1) {  // destination columns x0 + 1 .. x0 + C
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, w[k][NW - 1], 1);
+            uint32_t o[NW];
+            o[0] = shift_pair(prev, w[k][0]);
+#pragma unroll
+            for (int j = 1; j < NW; ++j) o[j] = shift_pair(w[k][j - 1], w[k][j]);
             if (lane != 0) {
-                st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), o);
+                st_words<POL, NW>(dst + x0, o);
             } else {  // column x0 belongs to the cell left of the warp
-                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + x0 + 1), (unsigned short)(o.x >> 16));
-                st_pol<ST::kPol>(reinterpret_cast<unsigned int*>(dst + x0 + 2), o.y);
-                st_pol<ST::kPol>(reinterpret_cast<uint2*>(dst + x0 + 4), make_uint2(o.z, o.w));
+                st_pol<POL>(reinterpret_cast<unsigned short*>(dst + x0 + 1), (unsigned short)(o[0] >> 16));
+                st_pol<POL>(reinterpret_cast<unsigned int*>(dst + x0 + 2), o[1]);
+                if constexpr (NW == 4) st_pol<POL>(reinterpret_cast<uint2*>(dst + x0 + 4), make_uint2(o[2], o[3]));
             }
             if (lane == 31)
-                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + xr), (unsigned short)(w[k][3] >> 16));
-        } else {                  // destination columns x0 - 1 .. x0 + 6
+                st_pol<POL>(reinterpret_cast<unsigned short*>(dst + xr), (unsigned short)(w[k][NW - 1] >> 16));
+        } else {                  // destination columns x0 - 1 .. x0 + C - 2
             const uint32_t next = __shfl_down_sync(0xffffffffu, w[k][0], 1);
-            const uint4 o = make_uint4(shift_pair(w[k][0], w[k][1]), shift_pair(w[k][1], w[k][2]),
-                                       shift_pair(w[k][2], w[k][3]), shift_pair(w[k][3], next));
+            uint32_t o[NW];
+#pragma unroll
+            for (int j = 0; j < NW - 1; ++j) o[j] = shift_pair(w[k][j], w[k][j + 1]);
+            o[NW - 1] = shift_pair(w[k][NW - 1], next);
             if (lane != 31) {
-                st_pol<ST::kPol>(reinterpret_cast<uint4*>(dst + x0), o);
-            } else {  // column x0 + 7 belongs to the cell right of the warp
-                st_pol<ST::kPol>(reinterpret_cast<uint2*>(dst + x0), make_uint2(o.x, o.y));
-                st_pol<ST::kPol>(reinterpret_cast<unsigned int*>(dst + x0 + 4), o.z);
-                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + x0 + 6), (unsigned short)(o.w & 0xFFFFu));
+                st_words<POL, NW>(dst + x0, o);
+            } else {  // column x0 + C - 1 belongs to the cell right of the warp
+                if constexpr (NW == 4) {
+                    st_pol<POL>(reinterpret_cast<uint2*>(dst + x0), make_uint2(o[0], o[1]));
+                    st_pol<POL>(reinterpret_cast<unsigned int*>(dst + x0 + 4), o[2]);
+                    st_pol<POL>(reinterpret_cast<unsigned short*>(dst + x0 + 6), (unsigned short)(o[3] & 0xFFFFu));
+                } else {
+                    st_pol<POL>(reinterpret_cast<unsigned int*>(dst + x0), o[0]);
+                    st_pol<POL>(reinterpret_cast<unsigned short*>(dst + x0 + 2), (unsigned short)(o[1] & 0xFFFFu));
+                }
             }
             if (lane == 0)
-                st_pol<ST::kPol>(reinterpret_cast<unsigned short*>(dst + xl), (unsigned short)(w[k][0] & 0xFFFFu));
+                st_pol<POL>(reinterpret_cast<unsigned short*>(dst + xl), (unsigned short)(w[k][0] & 0xFFFFu));
         }
     }
 }
@@ -1074,12 +1101,14 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
         // a pure tile (every cell fluid, in the grid, away from boundaries)
         // takes the pair path without reading its mask
         const bool pure = (te.y & TILE_PURE) != 0;
-        if (sizeof(typename ST::T) == 2 && shape.tw == VEC16_TILE_W) {
-            // 16-bit storage, eight cells per lane (blockDim.x == 32): plain
-            // steps of rows whose 256 cells are all interior take the vector
-            // path; the others, and observing steps, take four 64-cell pair rows
-            const int x0 = te.z + VEC16_CELLS * threadIdx.x;
-            const bool v16_ok = !OBS && (sd.nx % VEC16_CELLS) == 0;
+        const int V16 = sizeof(typename ST::T) == 2 ? vec16_cells(shape.tw) : 0;
+        if (V16 > 0) {
+            // 16-bit storage, V16 = 8 or 4 cells per lane (blockDim.x == 32):
+            // plain steps of rows whose 32 V16 cells are all interior take the
+            // vector path; the others, and observing steps, take V16 / 2
+            // 64-cell pair rows
+            const int x0 = te.z + V16 * threadIdx.x;
+            const bool v16_ok = !OBS && (sd.nx % (V16 > 0 ? V16 : 1)) == 0;
             for (int r = 0; r < rpt; ++r) {
                 const int y = te.w + threadIdx.y + r * blockDim.y;
                 bool fast = false;
@@ -1090,19 +1119,25 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
                             fast = true;
                         } else {
                             uint64_t m8 = ~0ull;
-                            if (y < sd.ny && x0 + VEC16_CELLS <= sd.nx)
-                                m8 = __ldg(reinterpret_cast<const unsigned long long*>(sd.mask + (int64_t)y * sd.nx + x0));
-                            fast = __all_sync(0xffffffffu, (m8 & 0x0E0E0E0E0E0E0E0Eull) == 0ull);
+                            const int64_t mo = (int64_t)y * sd.nx + x0;
+                            if (y < sd.ny && x0 + V16 <= sd.nx)
+                                m8 = V16 == 8 ? __ldg(reinterpret_cast<const unsigned long long*>(sd.mask + mo))
+                                              : (uint64_t)__ldg(reinterpret_cast<const unsigned int*>(sd.mask + mo));
+                            const uint64_t busy = V16 == 8 ? 0x0E0E0E0E0E0E0E0Eull : 0x0E0E0E0Eull;
+                            fast = __all_sync(0xffffffffu, (m8 & busy) == 0ull);
                             if (sd.tm_model == 0)
 #pragma unroll
-                                for (int j = 0; j < VEC16_CELLS; ++j) por |= (uint32_t)((m8 >> (8 * j)) & 1u) << j;
+                                for (int j = 0; j < 8; ++j) por |= (uint32_t)((m8 >> (8 * j)) & 1u) << j;
                         }
-                        if (fast) update_vec16_interior<ST, PAR>(sd, x0, y, por);
+                        if (fast) {
+                            if (V16 == 8) update_vec16_interior<ST, PAR, 4>(sd, x0, y, por);
+                            else update_vec16_interior<ST, PAR, 2>(sd, x0, y, por);
+                        }
                     }
                 }
                 if (!fast) {
 #pragma unroll 1
-                    for (int s = 0; s < VEC16_CELLS / 2; ++s)
+                    for (int s = 0; s < V16 / 2; ++s)
                         pair_row<ST, OBS, PAR, A>(sd, te.z + 64 * s + 2 * (int)threadIdx.x, y, pure, vec_ok, mode, acc);
                 }
             }
@@ -1555,8 +1590,10 @@ __global__ void __launch_bounds__(WS_THREADS, LBM_WS_MINB) step_kernel_ws(const 
 // pre-collision state, with per-thread and per-warp partials of type A: FP64
 // for observe-only reads, the storage's accumulator type for the steady-state
 // check step (which also writes).
-template <class ST, bool OBS, class A = double>
-__global__ void __launch_bounds__(256, OBS ? 2 : step_min_blocks<ST>()) step_kernel(const InstDesc* __restrict__ insts,
+// MB > 0: resident blocks of 256 threads to compile for (a register budget
+// chosen per launch geometry), else the storage's default
+template <class ST, bool OBS, class A = double, int MB = 0>
+__global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<ST>())) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
@@ -1647,8 +1684,8 @@ __device__ __forceinline__ void flow_wait(const int* done, int target, int* flag
     atomicExch(flags, 1);
 }
 
-template <class ST>
-__global__ void __launch_bounds__(256, flow_min_blocks<ST>())
+template <class ST, int MB = 0>
+__global__ void __launch_bounds__(256, MB > 0 ? MB : flow_min_blocks<ST>())
     step_kernel_flow(const InstDesc* __restrict__ insts, const FlowArgs fa, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;

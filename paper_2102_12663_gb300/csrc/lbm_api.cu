@@ -187,6 +187,7 @@ struct lbm_domain {
     // FP64 (bit parity with a plain evaluation).
     double p_ref = 0.0;
     double pin_pref[2] = {0.0, 0.0};  // p_ref of the interval in each pinned slot
+    int checks_since_recenter = -1;   // steady-state checks since the last move of p_ref (-1: never)
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS plain steps from an even step
     std::vector<int4> htiles;         // host copy of the tile list
     std::vector<int> hnbr;            // host copy of the neighbour lists
@@ -204,8 +205,8 @@ static constexpr int GRAPH_STEPS = 32;
 // the threads of a block: at most 256)
 static bool launch_ok(const lbm_launch& l, int prec) {
     const bool tw_ok = l.tile_w == 32 || l.tile_w == 64 || l.tile_w == 128 || l.tile_w == 256;
-    const bool rows_ok = cells_per_thread(prec, l.tile_w) == VEC16_CELLS ? l.block_rows <= 256 / 32
-                                                                          : l.tile_w * l.block_rows <= 256;
+    const bool rows_ok = cells_per_thread(prec, l.tile_w) >= 4 ? l.block_rows <= 256 / 32
+                                                                : l.tile_w * l.block_rows <= 256;
     return tw_ok && l.block_rows >= 1 && l.rows_per_thread >= 1 && l.rows_per_thread <= 64 && rows_ok &&
            (int64_t)l.tile_w * l.block_rows * l.rows_per_thread >= MIN_TILE_AREA &&
            l.blocks_per_sm >= 0 && l.blocks_per_sm <= 32 &&
@@ -1013,6 +1014,7 @@ extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
     set_heat_encoding(d);
     // the initial state f = feq(p_out, 0) is all zeros relative to p_ref = p_out
     d->p_ref = d->prec == LBM_F64 ? 0.0 : d->params.p_out;
+    d->checks_since_recenter = -1;
     d->h.pd.p_out = d->params.p_out - d->p_ref;
     d->h.pf.p_out = (float)d->h.pd.p_out;
     d->h.snap_valid = 0;
@@ -1233,11 +1235,16 @@ static constexpr int PIN_SLOT = NOBS + 1;  // doubles per slot (last: status wor
 // steady-state check whose IOP lies more than PREF_TOL of it away from p_ref,
 // the stored populations move to p_ref = IOP.  One pass over them, enqueued
 // after whatever is already queued on the domain's stream (d->step, and so
-// the parity, already counts that work).
-static constexpr double PREF_TOL = 0.05;
+// the parity, already counts that work).  While the IOP still rises it moves
+// at most once every PREF_EVERY checks, so the pass costs at most one step in
+// PREF_EVERY intervals.
+static constexpr double PREF_TOL = 0.01;
+static constexpr int PREF_EVERY = 20;
 static lbm_status maybe_recenter(lbm_domain* d, double iop) {
     if (d->prec == LBM_F64 || !std::isfinite(iop)) return LBM_OK;
+    if (d->checks_since_recenter >= 0 && ++d->checks_since_recenter < PREF_EVERY) return LBM_OK;
     if (std::fabs(iop - d->p_ref) <= PREF_TOL * std::fabs(iop)) return LBM_OK;
+    d->checks_since_recenter = 0;
     DISPATCH(d->prec, shift_pressure_kernel, d->d_desc, (int)(d->step & 1), iop - d->p_ref);
     CK(cudaGetLastError());
     d->p_ref = iop;
@@ -1558,6 +1565,9 @@ struct lbm_batch {
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     int ntiles = 0;
     bool dirty = true;
+    // per-step launches take the tiles holding boundary cells (the slower
+    // general update) first, then the pure tiles; the autotuner tries both
+    bool boundary_first = false;
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -1686,6 +1696,9 @@ static lbm_status batch_rebuild(lbm_batch* b) {
         }
     }
     if ((int64_t)tiles.size() > b->max_tiles) return fail(LBM_EBUSY, "batch tile capacity exceeded");
+    if (b->boundary_first) {  // per-step order only: the dataflow items keep their wavefront order
+        std::stable_partition(tiles.begin(), tiles.end(), [](const int4& t) { return !(t.y & TILE_PURE); });
+    }
     if (!tiles.empty()) {
         CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            b->stream));
@@ -1879,25 +1892,34 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     lbm_launch best = b->launch;
+    bool best_bfirst = b->boundary_first;
     lbm_status st = LBM_OK;
     for (const lbm_launch& c : cand) {
         if (!launch_ok(c, b->prec)) continue;  // a shape of another storage
-        if ((st = lbm_batch_set_launch(b, &c)) != LBM_OK) {
-            if (st == LBM_EBUSY) { st = LBM_OK; continue; }  // shape needs more tiles than fit
-            break;
+        // one launch per step: raster order and boundary tiles first
+        for (int order = 0; order < (c.stepping == LBM_STEP_PER_LAUNCH ? 2 : 1) && st == LBM_OK; ++order) {
+            b->boundary_first = order == 1;
+            b->dirty = true;
+            if ((st = lbm_batch_set_launch(b, &c)) != LBM_OK) {
+                if (st == LBM_EBUSY) st = LBM_OK;  // shape needs more tiles than fit
+                break;
+            }
+            if ((st = lbm_batch_step(b, 2)) != LBM_OK) break;  // warm-up, builds the tile list
+            cudaEventRecord(e0, b->stream);
+            if ((st = lbm_batch_step(b, steps_per_candidate)) != LBM_OK) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = c; best_bfirst = b->boundary_first; }
         }
-        if ((st = lbm_batch_step(b, 2)) != LBM_OK) break;  // warm-up, builds the tile list
-        cudaEventRecord(e0, b->stream);
-        if ((st = lbm_batch_step(b, steps_per_candidate)) != LBM_OK) break;
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = c; }
+        if (st != LBM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
+    b->boundary_first = best_bfirst;
+    b->dirty = true;
     if ((st = lbm_batch_set_launch(b, &best)) != LBM_OK) return st;
     if (chosen) *chosen = best;
     return LBM_OK;

@@ -126,12 +126,13 @@ struct Shape {
 
 // Cells per thread along x: the FP32-arithmetic kernels take cell pairs
 // (vector loads and stores, warp shuffles), the FP64 kernel single cells, and
-// the 16-bit storages on 256-cell tile rows eight cells (one 16-byte vector
-// per plane).
-constexpr int VEC16_CELLS = 8;
-constexpr int VEC16_TILE_W = 32 * VEC16_CELLS;
+// the 16-bit storages on 256- or 128-cell tile rows eight or four cells (one
+// 16- or 8-byte vector per plane; 32 threads per row).
+__host__ __device__ constexpr int vec16_cells(int tile_w) {
+    return tile_w == 256 ? 8 : (tile_w == 128 ? 4 : 0);
+}
 __host__ __device__ constexpr int cells_per_thread(int precision, int tile_w) {
-    return precision == 0 ? 1 : ((precision >= 2 && tile_w == VEC16_TILE_W) ? VEC16_CELLS : 2);
+    return precision == 0 ? 1 : ((precision >= 2 && vec16_cells(tile_w) > 0) ? vec16_cells(tile_w) : 2);
 }
 
 // ---- storage traits --------------------------------------------------------

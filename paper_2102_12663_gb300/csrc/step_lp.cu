@@ -42,7 +42,15 @@ static StepPlan plan_t(int mode, Shape shape) {
     } else {
         // the steady-state check step (observe and write) folds its partials
         // in FP32 per warp; observe-only reads keep FP64 partials
-        p.func = !obs ? reinterpret_cast<const void*>(&step_kernel<ST, false>)
+        // 16-bit storages: the eight-cell vector path (256-wide tiles) keeps 13
+        // planes of four packed words live and is built for 2 blocks of 256
+        // threads (128 registers); the other shapes for 3 (85 registers: more
+        // warps to hide memory latency)
+        const void* plain = reinterpret_cast<const void*>(&step_kernel<ST, false>);
+        if (sizeof(typename ST::T) == 2)
+            plain = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel<ST, false, double, 2>)
+                                    : reinterpret_cast<const void*>(&step_kernel<ST, false, double, 3>);
+        p.func = !obs ? plain
                  : (mode & OBS_WRITE) ? reinterpret_cast<const void*>(&step_kernel<ST, true, typename ST::A>)
                                       : reinterpret_cast<const void*>(&step_kernel<ST, true>);
         p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
@@ -63,6 +71,9 @@ template <class ST>
 static StepPlan flow_t(Shape shape) {
     StepPlan p;
     p.func = reinterpret_cast<const void*>(&step_kernel_flow<ST>);
+    if (sizeof(typename ST::T) == 2)
+        p.func = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel_flow<ST, 2>)
+                                 : reinterpret_cast<const void*>(&step_kernel_flow<ST, 3>);
     p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
     p.smem = 0;
     return p;

@@ -18,6 +18,9 @@ domain, one after the other, through lbm_run_to_steady.
 A request may carry its own steady tolerance (the 16-bit storages settle on
 a residual noise floor above the FP32 criterion) and its own step cap
 (workloads.steady_step_cap: a number of decay times of its slowest mode).
+With refine_tol, a 16-bit request that meets its own tolerance moves to the
+FP32 batch and finishes there to the FP32 criterion: the fast transient runs
+in 16-bit storage, and the result has the FP32 loop's accuracy.
 
 This module only orchestrates; every step of every solve runs in the CUDA
 library.
@@ -57,6 +60,7 @@ class Result:
     arrival_s: float
     admit_s: float
     finish_s: float
+    refined_steps: int = 0  # steps taken in FP32 after the request's own storage met its tolerance
 
     @property
     def latency_s(self) -> float:
@@ -92,7 +96,13 @@ def domain_bytes(req: Request) -> int:
 class Server:
     def __init__(self, budget_bytes: float = 150e9, tol: float = 1e-7, check_every: int = 100,
                  max_steps: int = 20000, max_instances: int = 64, max_tiles: int = 1 << 21,
-                 launch: dict | None = None, autotune: bool = False, device=None, stream=None):
+                 launch: dict | None = None, autotune: bool = False, device=None, stream=None,
+                 refine_tol: dict | None = None):
+        """refine_tol: {storage: tol}.  A request of such a storage that meets
+        its own tolerance is not retired: its state moves (on the device) to an
+        FP32 domain, which runs on to `tol` of the storage (the 16-bit
+        storages' residual settles above the FP32 criterion, so the fast
+        transient runs in 16-bit and the end of the approach in FP32)."""
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -109,6 +119,8 @@ class Server:
         self.results = []
         self.ticks = 0
         self.cell_updates = 0
+        self.refine_tol = dict(refine_tol or {})
+        self.refined = {}  # id -> steps taken before refinement
 
     def _batch(self, precision: str):
         if precision not in self.batches:
@@ -150,18 +162,57 @@ class Server:
         for rid in list(self.active):
             req, dom, nbytes, t_admit = self.active[rid]
             o = dom.last_observables()
-            tol = self.tol if req.tol is None else req.tol
+            refining = rid in self.refined
+            prec = "f32" if refining else req.precision
+            done_before = self.refined.get(rid, 0)
+            if refining:
+                tol = self.refine_tol[req.precision]
+            else:
+                tol = self.tol if req.tol is None else req.tol
             cap = self.max_steps if req.max_steps is None else req.max_steps
             converged = 0.0 <= o["residual"] < tol
             unstable = bool(o["nan_flag"])
-            if converged or unstable or dom.step_count >= cap:
-                b = self.batches[req.precision]
-                b.remove(dom)
-                self.results.append(Result(req.id, req.precision, req.nx, req.ny, dom.step_count,
-                                           converged, unstable, o, req.arrival_s, t_admit, t))
+            steps = done_before + dom.step_count
+            if converged and not refining and req.precision in self.refine_tol and steps < cap:
+                # (without room in the FP32 batch or the budget it keeps going
+                # in its own storage and tries again at the next check)
+                if self._refine(rid, req, dom, nbytes, t_admit, steps):
+                    continue
+                converged = False
+            if converged or unstable or steps >= cap:
+                self.batches[prec].remove(dom)
+                self.results.append(Result(req.id, req.precision, req.nx, req.ny, steps,
+                                           converged, unstable, o, req.arrival_s, t_admit, t,
+                                           refined_steps=dom.step_count if refining else 0))
                 dom.close()
                 del self.active[rid]
+                self.refined.pop(rid, None)
                 self.used -= nbytes
+
+    def _refine(self, rid, req, dom, nbytes, t_admit, steps) -> bool:
+        """Moves a request's state to an FP32 domain of the FP32 batch (device
+        copies through FP64 tensors: populations read back and written again).
+        False, and nothing done, while that batch or the budget has no room."""
+        nb = domain_bytes(dataclasses.replace(req, precision="f32"))
+        b32 = self.batches.get("f32")
+        if (b32 is not None and len(b32) >= self.max_instances) or self.used + nb - nbytes > self.budget:
+            return False
+        with self.torch.cuda.stream(self.stream):
+            f, g = dom.populations()
+            nd = lbm.Domain(dict(nx=req.nx, ny=req.ny, angle_deg=req.angle_deg), precision="f32",
+                            device=self.device, stream=self.stream)
+            nd.set_launch(**self.launch)
+            nd.set_params(req.params)
+            nd.write_populations(f, g)
+            del f, g
+        self.batches[req.precision].remove(dom)
+        dom.close()
+        self.used += nb - nbytes
+        self.peak_used = max(self.peak_used, self.used)
+        self._batch("f32").add(nd)
+        self.active[rid] = (req, nd, nb, t_admit)
+        self.refined[rid] = steps
+        return True
 
     def run(self, requests, realtime: bool = True) -> list:
         """Serve `requests`; arrival times are honoured against the wall clock

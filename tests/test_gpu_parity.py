@@ -462,6 +462,7 @@ def test_fp32_observables_any_block_width(launch):
 VEC16_SHAPES = [
     dict(tile_w=256, block_rows=2, rows_per_thread=2, blocks_per_sm=0, stepping=lbm.STEP_PER_LAUNCH),
     dict(tile_w=256, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=lbm.STEP_FLOW),
+    dict(tile_w=128, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=lbm.STEP_PER_LAUNCH),
 ]
 
 
@@ -469,13 +470,14 @@ VEC16_SHAPES = [
 @pytest.mark.parametrize("nx,ny", [(512, 256), (520, 130), (516, 130)])
 @pytest.mark.parametrize("launch", range(len(VEC16_SHAPES)))
 def test_vector16_path_eye(prec, unit_roundoff, nx, ny, launch):
-    """The eight-cell vector path of the 16-bit storages (256-cell tile rows,
-    one 16-byte vector per plane and lane) against the FP64 oracle after an
+    """The vector paths of the 16-bit storages (eight cells and one 16-byte
+    vector per plane and lane on 256-cell tile rows, four cells and 8-byte
+    vectors on 128-cell rows) against the FP64 oracle after an
     odd and an even number of steps (a few unit roundoffs times sqrt(n), as
     for the pair path), and against the pair-path shape within the same
     bound.  512 x 256 has whole interior rows; 520 x 130 ends in a partial
     tile (the last segment falls back to cell pairs); 516 x 130 is no multiple
-    of eight columns (every row falls back)."""
+    of eight columns (every eight-cell row falls back; four-cell rows do not)."""
     dom, ref, _ = eye_pair(nx, ny, prec, launch=VEC16_SHAPES[launch])
     pair, _, _ = eye_pair(nx, ny, prec, launch=dict(tile_w=64, block_rows=4, rows_per_thread=1))
     done = 0
