@@ -141,25 +141,27 @@ def eye_params():
     return W.config_params(W.CONFIG_FP32)
 
 
-def oracle_sample(seconds_budget: float = 15.0, threads: int | None = None):
-    """Times the FP64 C oracle on the 4096 x 2048 eye: a bounded number of
-    steps after initialisation.  Returns (MLUPS over active cells, steps,
-    cores, seconds)."""
-    import numpy as np
-
+def oracle_sample(seconds_budget: float = 15.0, threads: int | None = None, nx: int = NX, ny: int = NY,
+                  params: dict | None = None, angle_deg: float = 45.0):
+    """Times the FP64 C oracle on an eye (default the 4096 x 2048 one): after
+    initialisation and one step, chunks of steps until seconds_budget has
+    passed.  Returns (MLUPS over active cells, steps, cores, seconds)."""
     import oracle as O
     threads = threads or os.cpu_count() or 1
     O.set_threads(threads)
-    m, g = O.eye_mask(NX, NY, 45.0)
+    m, g = O.eye_mask(nx, ny, angle_deg)
     n_active = int(((m == 0) | (m == 1)).sum())
-    st = O.State(g, O.make_params(**eye_params()), m)
-    t0 = time.perf_counter()
+    st = O.State(g, O.make_params(**(params or eye_params())), m)
     st.run(1)
-    one = time.perf_counter() - t0
-    steps = max(1, int(seconds_budget / max(one, 1e-3)))
-    t0 = time.perf_counter()
-    st.run(steps)
-    dt = time.perf_counter() - t0
+    steps, dt, chunk = 0, 0.0, 1
+    while dt < seconds_budget:
+        t0 = time.perf_counter()
+        st.run(chunk)
+        took = time.perf_counter() - t0
+        steps += chunk
+        dt += took
+        # next chunk: about a quarter of the remaining budget
+        chunk = max(1, int(0.25 * max(seconds_budget - dt, 0.0) / max(took / chunk, 1e-7)))
     del st
     return n_active * steps / dt / 1e6, steps, threads, dt
 
@@ -315,11 +317,23 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups_cpu, steps_cpu, cores, dt = oracle_sample(seconds_budget=12.0)
         mlups_1, steps_1, _, dt_1 = oracle_sample(seconds_budget=4.0, threads=1)
+        from paper_2102_12663_gb300 import workloads as W
+        other = {}
+        for name, (cfgd, nx, ny) in {"fp64_160x80": (W.CONFIG_FP64, 160, 80),
+                                     "fp32_downscale_512x256": (W.CONFIG_FP32, 512, 256),
+                                     "precision_check_1024x512": (W.CONFIG_PRECISION, 1024, 512)}.items():
+            pp = W.config_params(cfgd, ny=ny)
+            ang = cfgd["angle_deg"]
+            all_c = oracle_sample(seconds_budget=1.5, nx=nx, ny=ny, params=pp, angle_deg=ang)
+            one_c = oracle_sample(seconds_budget=1.5, threads=1, nx=nx, ny=ny, params=pp, angle_deg=ang)
+            other[name] = {"mlups_all_cores": all_c[0], "mlups_one_core": one_c[0],
+                           "steps": [all_c[1], one_c[1]]}
         cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps_cpu} time steps of the 4096x2048 eye ({dt:.1f} s, FP64, OpenMP rows)",
                "cpu_model": cpu_model(),
                "single_thread": {"value": mlups_1, "unit": "MLUPS", "cores": 1,
-                                 "sample": f"{steps_1} time steps of the same eye ({dt_1:.1f} s)"}}
+                                 "sample": f"{steps_1} time steps of the same eye ({dt_1:.1f} s)"},
+               "other_grids": other}
     if rank == 0:
         line = {
             "metric": "coupled MLUPS (active cells)", "value": value, "unit": "MLUPS",
