@@ -604,16 +604,28 @@ __device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int
 
 // Flow collision (Eqs. 6-9, 15-17), Darcy drag (Eq. 4) and heat collision
 // (Eqs. 11-13) of one interior cell, in place: q = 0..8 flow, 9..12 T_1..T_4.
-__device__ __forceinline__ void collide_interior(float* f, bool porous, const Phys<float>& ph) {
+// LOG2S: the flow values come and go scaled by S = 2^LOG2S (as a 16-bit
+// storage holds them).  Every intermediate of the flow collision is then S
+// times, or for the square of the velocity S^2 times, the unscaled one, with
+// the same rounding: the constants that meet a product of two scaled values
+// carry 1/S, the force terms S.  TCODE: the heat deviations come and go in
+// code units (value * Tscale, the 16-bit storages' heat codes), with the
+// run's constants gbc, dT0c, Trefc; else in the units of T.
+template <int LOG2S = 0, bool TCODE = false>
+__device__ __forceinline__ void collide_interior(float* f, bool porous, const InstDesc& d) {
+    const Phys<float>& ph = d.pf;
+    constexpr float S = float(1 << LOG2S), iS = 1.0f / float(1 << LOG2S);
     const float ux = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     const float uy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     const float usq = ux * ux + uy * uy;
     const float e5 = ux + uy, e6 = uy - ux;
     // even parts w_i (4.5 (e_i.u)^2 - 1.5 |u|^2) of S_i, one per opposite pair
-    const float h1 = float(4.5 * K_W1) * ux * ux - float(1.5 * K_W1) * usq;
-    const float h2 = float(4.5 * K_W1) * uy * uy - float(1.5 * K_W1) * usq;
-    const float h5 = float(4.5 * K_W5) * e5 * e5 - float(1.5 * K_W5) * usq;
-    const float h6 = float(4.5 * K_W5) * e6 * e6 - float(1.5 * K_W5) * usq;
+    constexpr float a1 = float(4.5 * K_W1) * iS, b1 = float(1.5 * K_W1) * iS;
+    constexpr float a5 = float(4.5 * K_W5) * iS, b5 = float(1.5 * K_W5) * iS;
+    const float h1 = a1 * ux * ux - b1 * usq;
+    const float h2 = a1 * uy * uy - b1 * usq;
+    const float h5 = a5 * e5 * e5 - b5 * usq;
+    const float h6 = a5 * e6 * e6 - b5 * usq;
     // S_0 = -sum_{i>=1} S_i (the S_i of Eq. 8 sum to zero), from the rounded even parts
     const float S0 = -2.0f * ((h1 + h2) + (h5 + h6));
     const float sum18 = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
@@ -632,10 +644,10 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const Ph
     const float q6 = pdg + h6, o6 = float(3.0 * K_W5) * e6;
     const float feq0 = -P4 + S0;
     // body force F = drive - g beta (T - T0) g_hat; F_i = (1/2) e_i . F on the axis links
-    const float gb = ph.g_beta * (Tm - ph.dT0);
+    const float gb = TCODE ? d.gbc * (Tm - d.dT0c) : ph.g_beta * (Tm - ph.dT0);
     const float Fx = ph.drive_x - gb * ph.gx;
     const float Fy = ph.drive_y - gb * ph.gy;
-    const float F1 = 0.5f * Fx, F2 = 0.5f * Fy;
+    const float F1 = (0.5f * S) * Fx, F2 = (0.5f * S) * Fy;
     // Non-equilibrium parts n_i = f_i - feq_i (exact subtractions: f_i and
     // feq_i are close).  Their sum vanishes in exact arithmetic (the
     // equilibrium carries the cell's mass sum_{i>=1} f_i, Eq. 9), but the
@@ -659,23 +671,26 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const Ph
     f[6] = f[6] - om * (n6 - nm);
     f[8] = f[8] - om * (n8 - nm);
     if (porous) {
-        const float umx = (ux + 0.5f * Fx) / ph.den;
-        const float umy = (uy + 0.5f * Fy) / ph.den;
+        // mid-step velocity (u + F/2) / (1 + nu / (2K)), F1 = S Fx / 2
+        const float umx = (ux + F1) / ph.den;
+        const float umy = (uy + F2) / ph.den;
         const float FDx = -ph.cK * umx, FDy = -ph.cK * umy;
-        const float a1 = float(3.0 * K_W1), a5 = float(3.0 * K_W5);
-        f[1] += a1 * FDx;
-        f[3] -= a1 * FDx;
-        f[2] += a1 * FDy;
-        f[4] -= a1 * FDy;
-        f[5] += a5 * (FDx + FDy);
-        f[7] -= a5 * (FDx + FDy);
-        f[6] += a5 * (FDy - FDx);
-        f[8] -= a5 * (FDy - FDx);
+        const float c1 = float(3.0 * K_W1), c5 = float(3.0 * K_W5);
+        f[1] += c1 * FDx;
+        f[3] -= c1 * FDx;
+        f[2] += c1 * FDy;
+        f[4] -= c1 * FDy;
+        f[5] += c5 * (FDx + FDy);
+        f[7] -= c5 * (FDx + FDy);
+        f[6] += c5 * (FDy - FDx);
+        f[8] -= c5 * (FDy - FDx);
     }
     // heat: the same for the D2Q4 populations, whose equilibria carry T.  They
     // are stored and collided as deviations from Tref/4, so their rounding is
-    // that of T - Tref: T_i^eq - Tref/4 = (T - Tref)/4 + (T/2) e_i.u
-    const float omT = ph.omegaT, Tq = 0.25f * Tm, Th = 0.5f * (Tm + ph.Tref);
+    // that of T - Tref: T_i^eq - Tref/4 = (T - Tref)/4 + (T/2) e_i.u (the
+    // velocity's scale S taken out of T/2)
+    const float omT = ph.omegaT, Tq = 0.25f * Tm;
+    const float Th = (0.5f * iS) * (Tm + (TCODE ? d.Trefc : ph.Tref));
     const float m1 = f[9] - (Tq + Th * ux), m3 = f[11] - (Tq - Th * ux);
     const float m2 = f[10] - (Tq + Th * uy), m4 = f[12] - (Tq - Th * uy);
     const float mm = ((m1 + m3) + (m2 + m4)) * 0.25f;
@@ -701,8 +716,8 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
     const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
     const int xl = x == 0 ? nx - 1 : x - 1;
     const int xr = x + 2 == nx ? 0 : x + 2;
-    collide_interior(a, por0, d.pf);
-    collide_interior(b, por1, d.pf);
+    collide_interior(a, por0, d);
+    collide_interior(b, por1, d);
 
     // ---- store --------------------------------------------------------------
     if (PAR == 0) {
@@ -895,7 +910,10 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
 // x-shifted links are assembled from the neighbouring lane's words (one
 // shuffle per plane and __byte_perm), and the warp's first and last lanes
 // load or store the one code outside the warp's 256 cells.  Same model and
-// arithmetic as the pair path (collide_interior).
+// operations as the pair path (collide_interior), run on the values as
+// stored: the flow populations with their power-of-two scale (the same
+// rounding as unscaled), the heat deviations in code units, so that decoding
+// and encoding are bare conversions (and the heat codes' clamp of the knee).
 
 // the code pair (b of lo, a of hi): word whose low half is the high half of
 // lo and whose high half is the low half of hi (a one-code shift)
@@ -981,25 +999,26 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
 #pragma unroll 1
     for (int q = 0; q < NW; ++q) {
         float a[13], b[13];
+        // flow values as stored (scaled by 2^kLog2S), heat in code units
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            const float2 v = ST::decf2(w[k][0], d);
+            const float2 v = ST::decf2_raw(w[k][0]);
             a[k] = v.x;
             b[k] = v.y;
         }
 #pragma unroll
         for (int k = 9; k < 13; ++k) {
-            const float2 v = ST::decT2(w[k][0], d);
+            const float2 v = dec_tcode2(w[k][0]);
             a[k] = v.x;
             b[k] = v.y;
         }
-        collide_interior(a, ((por >> (2 * q)) & 1u) != 0, d.pf);
-        collide_interior(b, ((por >> (2 * q + 1)) & 1u) != 0, d.pf);
+        collide_interior<ST::kLog2S, true>(a, ((por >> (2 * q)) & 1u) != 0, d);
+        collide_interior<ST::kLog2S, true>(b, ((por >> (2 * q + 1)) & 1u) != 0, d);
         uint32_t o[13];
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
             const int dst = PAR == 0 ? (k < 9 ? opp(k) : 8 + opp(k - 8)) : k;
-            o[dst] = k < 9 ? ST::encf2(a[k], b[k], d) : ST::encT2(a[k], b[k], d);
+            o[dst] = k < 9 ? ST::encf2_raw(a[k], b[k]) : enc_tcode2(a[k], b[k]);
         }
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
@@ -1384,8 +1403,8 @@ __device__ __forceinline__ void ws_segment(const InstDesc& d, const typename ST:
     }
     ws_load<ST, PAR>(d, stage, c, a, b);
     if (interior) {
-        collide_interior(a, por0, d.pf);
-        collide_interior(b, por1, d.pf);
+        collide_interior(a, por0, d);
+        collide_interior(b, por1, d);
         pair_store_lane<ST, PAR>(d, x, y, a, b);
         return;
     }
@@ -1603,15 +1622,20 @@ __global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<
     // programmatic dependent launch (graph replays): let the next step launch
     // now; its blocks wait below until this grid has completed
     grid_dependents_go();
+    int cur = -1;  // instance whose descriptor sd holds
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 te = tiles[t];
-        __syncthreads();
-        {
+        // te.x is the same for the whole block, so the barriers are taken by
+        // all of its threads or by none; an observing step also reuses red
+        // per tile, so it always synchronises
+        if (OBS || te.x != cur) {
+            __syncthreads();
             const uint64_t* src = reinterpret_cast<const uint64_t*>(insts + te.x);
             uint64_t* dst = reinterpret_cast<uint64_t*>(&sd);
             for (int k = tid; k < (int)(sizeof(InstDesc) / 8); k += nthreads) dst[k] = src[k];
+            __syncthreads();
+            cur = te.x;
         }
-        __syncthreads();
         // the previous step (if launched as our programmatic prerequisite) has
         // completed and its writes are visible before any population is touched
         grid_dependency_wait();

@@ -403,7 +403,17 @@ static lbm_status build_curved(lbm_domain* d) {
     return LBM_OK;
 }
 
+// The 16-bit vector path's constants in heat code units (value * Tscale),
+// from the descriptor's parameters and heat encoding.
+static void derive_code_units(InstDesc& h) {
+    h.gbc = (float)((double)h.pf.g_beta * (double)h.Tstep);
+    h.dT0c = (float)((double)h.pf.dT0 * (double)h.Tscale);
+    h.Trefc = (float)((double)h.pf.Tref * (double)h.Tscale);
+    h.pad2 = 0.0f;
+}
+
 static lbm_status upload_desc(lbm_domain* d) {
+    derive_code_units(d->h);
     CK(cudaMemcpyAsync(d->d_desc, &d->h, sizeof(InstDesc), cudaMemcpyHostToDevice, d->stream));
     return LBM_OK;
 }
@@ -1062,6 +1072,7 @@ static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int
         return e;
     }
     const StepPlan pl = step_plan(prec, 0, sh);
+    const int gsz = pl.max_grid > 0 ? std::min(grid, pl.max_grid) : grid;
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         const InstDesc* a0 = insts;
         const int4* a1 = tiles;
@@ -1072,7 +1083,7 @@ static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(pl.max_grid > 0 ? std::min(grid, pl.max_grid) : grid);
+        cfg.gridDim = dim3(gsz);
         cfg.blockDim = pl.block;
         cfg.dynamicSmemBytes = pl.smem;
         cfg.stream = cs;
@@ -1729,6 +1740,7 @@ static lbm_status batch_upload_table(lbm_batch* b) {
     b->htable.resize(b->members.size());
     for (size_t k = 0; k < b->members.size(); ++k) {
         InstDesc t = b->members[k]->h;
+        derive_code_units(t);
         t.parity = (int)(b->members[k]->step & 1);
         t.obs = b->d_obs + k * NOBS;
         b->htable[k] = t;

@@ -101,6 +101,11 @@ struct InstDesc {
     // 16-bit storages: heat deviations as 16-bit fixed point,
     // code = round(value * Tscale), value = code * Tstep
     float Tstep, Tscale;
+    // the same run's constants for the 16-bit vector path, whose collision
+    // takes the heat deviations in code units (value * Tscale): g beta Tstep,
+    // (T0 - Tref) Tscale and Tref Tscale (set from the fields above whenever
+    // the descriptor is uploaded)
+    float gbc, dT0c, Trefc, pad2;
 };
 // most blocks that fold one instance's tile partials
 constexpr int FOLD_MAX = 32;
@@ -158,20 +163,51 @@ __device__ __forceinline__ void st_pol(V* p, V v) {
 // a thermal boundary layer forms, anti-bounce-back at a wall of temperature
 // T_w returns deviations up to (T_w - T0)/2 - d*, up to 3/4 of span: the
 // outer codes cover them with a step TFIX_COARSE times coarser, out to about
-// span.  Codes saturate at +-32767.
+// span.  Codes saturate at the ends of the 16-bit range.
 constexpr float TFIX_KNEE = 24576.0f;
 constexpr float TFIX_COARSE = 8.0f;
+// In code units (value * Tscale): the code of q is q inside the knee and
+// knee + (|q| - knee) / 8 outside it, i.e. c = k + (q - k) / 8 with k = q
+// clamped to the knee; rounded to the nearest integer, saturated to the
+// 16-bit range (the float-to-integer conversion saturates).  The value of
+// code c is c + 7 (c - k), k = c clamped to the knee (exact in FP32).
+__device__ __forceinline__ float tcode_fold(float q) {
+    const float k = fminf(fmaxf(q, -TFIX_KNEE), TFIX_KNEE);
+    return fmaf(q - k, 1.0f / TFIX_COARSE, k);
+}
+__device__ __forceinline__ float tcode_unfold(float c) {
+    const float k = fminf(fmaxf(c, -TFIX_KNEE), TFIX_KNEE);
+    return fmaf(c - k, TFIX_COARSE - 1.0f, c);
+}
+// two codes from two values in code units (a in the low half)
+__device__ __forceinline__ uint32_t enc_tcode2(float a, float b) {
+    uint32_t w;
+    asm("{\n\t.reg .s16 lo, hi;\n\t"
+        "cvt.rni.s16.f32 lo, %1;\n\t"
+        "cvt.rni.s16.f32 hi, %2;\n\t"
+        "mov.b32 %0, {lo, hi};\n\t}"
+        : "=r"(w)
+        : "f"(tcode_fold(a)), "f"(tcode_fold(b)));
+    return w;
+}
+// the two values in code units of a word of two codes
+__device__ __forceinline__ float2 dec_tcode2(uint32_t w) {
+    float a, b;
+    asm("{\n\t.reg .s16 lo, hi;\n\t"
+        "mov.b32 {lo, hi}, %2;\n\t"
+        "cvt.rn.f32.s16 %0, lo;\n\t"
+        "cvt.rn.f32.s16 %1, hi;\n\t}"
+        : "=f"(a), "=f"(b)
+        : "r"(w));
+    return make_float2(tcode_unfold(a), tcode_unfold(b));
+}
 __device__ __forceinline__ unsigned int enc_tfix(float v, const InstDesc& d) {
-    const float q = v * d.Tscale;
-    const float a = fabsf(q);
-    const float over = fmaxf(a - TFIX_KNEE, 0.0f);
-    const float c = fminf(rintf(a - over + over * (1.0f / TFIX_COARSE)), 32767.0f);
-    return (unsigned int)(unsigned short)(short)(int)copysignf(c, q);
+    short c;
+    asm("cvt.rni.s16.f32 %0, %1;" : "=h"(c) : "f"(tcode_fold(v * d.Tscale)));
+    return (unsigned int)(unsigned short)c;
 }
 __device__ __forceinline__ float dec_tfix(unsigned int h, const InstDesc& d) {
-    const float c = (float)(short)(unsigned short)h;
-    const float over = fmaxf(fabsf(c) - TFIX_KNEE, 0.0f);
-    return (c + copysignf(over * (TFIX_COARSE - 1.0f), c)) * d.Tstep;
+    return tcode_unfold((float)(short)(unsigned short)h) * d.Tstep;
 }
 
 // Populations are read through L2 only: each slot is read once per step, and
@@ -219,8 +255,18 @@ struct StF16T {
     using R = float;
     using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
     static constexpr int kPol = POL;
+    // stored flow value = value * 2^kLog2S (the host's fscale)
+    static constexpr int kLog2S = 12;
     // packed pairs of 16-bit codes (the vector path): the lower column in the
-    // low half of a 32-bit word
+    // low half of a 32-bit word; the _raw forms convert the stored values
+    // without the scale (the vector path's collision takes them scaled)
+    static __device__ __forceinline__ uint32_t encf2_raw(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    static __device__ __forceinline__ float2 decf2_raw(uint32_t w) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    }
     static __device__ __forceinline__ uint32_t encf2(float a, float b, const InstDesc& d) {
         const __half2 h = __floats2half2_rn(a * d.fscale, b * d.fscale);
         return *reinterpret_cast<const uint32_t*>(&h);
@@ -245,10 +291,11 @@ struct StF16T {
     static __device__ __forceinline__ R sldf(const T* p, const InstDesc& d) { return __half2float(*p) * d.finv; }
     // heat deviations: 16-bit companded fixed point (enc_tfix / dec_tfix)
     static __device__ __forceinline__ uint32_t encT2(float a, float b, const InstDesc& d) {
-        return enc_tfix(a, d) | (enc_tfix(b, d) << 16);
+        return enc_tcode2(a * d.Tscale, b * d.Tscale);
     }
     static __device__ __forceinline__ float2 decT2(uint32_t w, const InstDesc& d) {
-        return make_float2(dec_tfix(w & 0xFFFFu, d), dec_tfix(w >> 16, d));
+        const float2 v = dec_tcode2(w);
+        return make_float2(v.x * d.Tstep, v.y * d.Tstep);
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
         return dec_tfix(__ldcg(reinterpret_cast<const unsigned short*>(p)), d);
@@ -272,6 +319,14 @@ struct StBF16T {
     using R = float;
     using A = float;  // per-thread and per-warp partials (tiles fold in FP64)
     static constexpr int kPol = POL;
+    static constexpr int kLog2S = 0;  // stored unscaled (fscale 1)
+    static __device__ __forceinline__ uint32_t encf2_raw(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    static __device__ __forceinline__ float2 decf2_raw(uint32_t w) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
     static __device__ __forceinline__ uint32_t encf2(float a, float b, const InstDesc& d) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a * d.fscale, b * d.fscale);
         return *reinterpret_cast<const uint32_t*>(&h);
@@ -298,10 +353,11 @@ struct StBF16T {
     }
     // heat deviations: 16-bit companded fixed point (enc_tfix / dec_tfix)
     static __device__ __forceinline__ uint32_t encT2(float a, float b, const InstDesc& d) {
-        return enc_tfix(a, d) | (enc_tfix(b, d) << 16);
+        return enc_tcode2(a * d.Tscale, b * d.Tscale);
     }
     static __device__ __forceinline__ float2 decT2(uint32_t w, const InstDesc& d) {
-        return make_float2(dec_tfix(w & 0xFFFFu, d), dec_tfix(w >> 16, d));
+        const float2 v = dec_tcode2(w);
+        return make_float2(v.x * d.Tstep, v.y * d.Tstep);
     }
     static __device__ __forceinline__ R ldT(const T* p, const InstDesc& d) {
         return dec_tfix(__ldcg(reinterpret_cast<const unsigned short*>(p)), d);
