@@ -700,6 +700,99 @@ __device__ __forceinline__ void collide_interior(float* f, bool porous, const In
     f[12] = f[12] - omT * (m4 - mm);
 }
 
+// The same collision for two cells at once, with Blackwell's paired FP32
+// operations (component x: one cell, y: the other; one instruction per pair
+// of operations, each component rounded as its scalar operation).  por: bit 0
+// the first cell is porous, bit 1 the second.  The Darcy drag multiplies by
+// the descriptor's 1 / den instead of dividing by den.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2(float s) { return make_float2(s, s); }
+
+template <int LOG2S = 0, bool TCODE = false>
+__device__ __forceinline__ void collide_interior2(float2* f, uint32_t por, const InstDesc& d) {
+    const Phys<float>& ph = d.pf;
+    constexpr float S = float(1 << LOG2S), iS = 1.0f / float(1 << LOG2S);
+    const float2 d13 = p2sub(f[1], f[3]), d24 = p2sub(f[2], f[4]);
+    const float2 d57 = p2sub(f[5], f[7]), d68 = p2sub(f[6], f[8]);
+    const float2 ux = p2add(d13, p2sub(d57, d68));
+    const float2 uy = p2add(d24, p2add(d57, d68));
+    const float2 usq = p2fma(ux, ux, p2mul(uy, uy));
+    const float2 e5 = p2add(ux, uy), e6 = p2sub(uy, ux);
+    // even parts w_i (4.5 (e_i.u)^2 - 1.5 |u|^2), one per opposite pair
+    constexpr float a1 = float(4.5 * K_W1) * iS, b1 = float(1.5 * K_W1) * iS;
+    constexpr float a5 = float(4.5 * K_W5) * iS, b5 = float(1.5 * K_W5) * iS;
+    const float2 t1 = p2mul(p2(-b1), usq), t5 = p2mul(p2(-b5), usq);
+    const float2 h1 = p2fma(p2mul(p2(a1), ux), ux, t1);
+    const float2 h2 = p2fma(p2mul(p2(a1), uy), uy, t1);
+    const float2 h5 = p2fma(p2mul(p2(a5), e5), e5, t5);
+    const float2 h6 = p2fma(p2mul(p2(a5), e6), e6, t5);
+    // S_0 = -sum_{i>=1} S_i from the rounded even parts
+    const float2 S0 = p2mul(p2(-2.0f), p2add(p2add(h1, h2), p2add(h5, h6)));
+    const float2 sum18 = p2add(p2add(p2add(f[1], f[3]), p2add(f[2], f[4])),
+                               p2add(p2add(f[5], f[7]), p2add(f[6], f[8])));
+    // pressure parts lambda p = P4 / 5, gamma p = P4 / 4 - lambda p (exact)
+    const float2 P4 = p2add(sum18, S0);
+    const float2 pax = p2mul(P4, p2(0.2f));
+    const float2 pdg = p2fma(P4, p2(0.25f), p2mul(pax, p2(-1.0f)));
+    const float2 Tm = p2add(p2add(f[9], f[11]), p2add(f[10], f[12]));
+    const float2 q1 = p2add(pax, h1), o1 = p2mul(p2(float(3.0 * K_W1)), ux);
+    const float2 q2 = p2add(pax, h2), o2 = p2mul(p2(float(3.0 * K_W1)), uy);
+    const float2 q5 = p2add(pdg, h5), o5 = p2mul(p2(float(3.0 * K_W5)), e5);
+    const float2 q6 = p2add(pdg, h6), o6 = p2mul(p2(float(3.0 * K_W5)), e6);
+    const float2 feq0 = p2sub(S0, P4);
+    // body force F = drive - g beta (T - T0) g_hat; F_i = S (1/2) e_i . F
+    const float2 gb = TCODE ? p2mul(p2(d.gbc), p2sub(Tm, p2(d.dT0c))) : p2mul(p2(ph.g_beta), p2sub(Tm, p2(ph.dT0)));
+    const float2 F1 = p2mul(p2(0.5f * S), p2fma(gb, p2(-ph.gx), p2(ph.drive_x)));
+    const float2 F2 = p2mul(p2(0.5f * S), p2fma(gb, p2(-ph.gy), p2(ph.drive_y)));
+    // non-equilibrium parts, their mean taken out before the relaxation
+    const float2 n1 = p2sub(f[1], p2add(q1, o1)), n3 = p2sub(f[3], p2sub(q1, o1));
+    const float2 n2 = p2sub(f[2], p2add(q2, o2)), n4 = p2sub(f[4], p2sub(q2, o2));
+    const float2 n5 = p2sub(f[5], p2add(q5, o5)), n7 = p2sub(f[7], p2sub(q5, o5));
+    const float2 n6 = p2sub(f[6], p2add(q6, o6)), n8 = p2sub(f[8], p2sub(q6, o6));
+    const float2 nm = p2mul(p2add(p2add(p2add(n1, n3), p2add(n2, n4)), p2add(p2add(n5, n7), p2add(n6, n8))),
+                            p2(0.125f));
+    const float2 mom = p2(-ph.omega);
+    f[0] = p2fma(mom, p2sub(f[0], feq0), f[0]);
+    f[1] = p2add(p2fma(mom, p2sub(n1, nm), f[1]), F1);
+    f[3] = p2sub(p2fma(mom, p2sub(n3, nm), f[3]), F1);
+    f[2] = p2add(p2fma(mom, p2sub(n2, nm), f[2]), F2);
+    f[4] = p2sub(p2fma(mom, p2sub(n4, nm), f[4]), F2);
+    f[5] = p2fma(mom, p2sub(n5, nm), f[5]);
+    f[7] = p2fma(mom, p2sub(n7, nm), f[7]);
+    f[6] = p2fma(mom, p2sub(n6, nm), f[6]);
+    f[8] = p2fma(mom, p2sub(n8, nm), f[8]);
+    if (por & 3u) {
+        // mid-step velocity (u + F/2) / den, drag -cK u_m on the porous cell(s) only
+        const float2 k = make_float2((por & 1u) ? -ph.cK * d.rden : 0.0f, (por & 2u) ? -ph.cK * d.rden : 0.0f);
+        const float2 FDx = p2mul(p2add(ux, F1), k), FDy = p2mul(p2add(uy, F2), k);
+        const float2 c1 = p2(float(3.0 * K_W1)), c5 = p2(float(3.0 * K_W5));
+        const float2 sp = p2add(FDx, FDy), sm = p2sub(FDy, FDx);
+        f[1] = p2fma(c1, FDx, f[1]);
+        f[3] = p2sub(f[3], p2mul(c1, FDx));
+        f[2] = p2fma(c1, FDy, f[2]);
+        f[4] = p2sub(f[4], p2mul(c1, FDy));
+        f[5] = p2fma(c5, sp, f[5]);
+        f[7] = p2sub(f[7], p2mul(c5, sp));
+        f[6] = p2fma(c5, sm, f[6]);
+        f[8] = p2sub(f[8], p2mul(c5, sm));
+    }
+    // heat: deviations from Tref/4, T_i^eq - Tref/4 = (T - Tref)/4 + (T/2) e_i.u
+    const float2 Tq = p2mul(p2(0.25f), Tm);
+    const float2 Th = p2mul(p2(0.5f * iS), p2add(Tm, p2(TCODE ? d.Trefc : ph.Tref)));
+    const float2 Tn = p2mul(p2(-0.5f * iS), p2add(Tm, p2(TCODE ? d.Trefc : ph.Tref)));
+    const float2 m1 = p2sub(f[9], p2fma(Th, ux, Tq)), m3 = p2sub(f[11], p2fma(Tn, ux, Tq));
+    const float2 m2 = p2sub(f[10], p2fma(Th, uy, Tq)), m4 = p2sub(f[12], p2fma(Tn, uy, Tq));
+    const float2 mm = p2mul(p2add(p2add(m1, m3), p2add(m2, m4)), p2(0.25f));
+    const float2 momT = p2(-ph.omegaT);
+    f[9] = p2fma(momT, p2sub(m1, mm), f[9]);
+    f[10] = p2fma(momT, p2sub(m2, mm), f[10]);
+    f[11] = p2fma(momT, p2sub(m3, mm), f[11]);
+    f[12] = p2fma(momT, p2sub(m4, mm), f[12]);
+}
+
 // Collision of a cell pair (cells x and x+1, 13 values each) and its AA-pattern
 // stores; every lane of the warp takes part (odd steps assemble x-shifted
 // links by shuffles).
@@ -998,27 +1091,18 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
     // inlined collisions) stays small enough for the instruction cache.
 #pragma unroll 1
     for (int q = 0; q < NW; ++q) {
-        float a[13], b[13];
+        float2 v[13];
         // flow values as stored (scaled by 2^kLog2S), heat in code units
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float2 v = ST::decf2_raw(w[k][0]);
-            a[k] = v.x;
-            b[k] = v.y;
-        }
+        for (int k = 0; k < 9; ++k) v[k] = ST::decf2_raw(w[k][0]);
 #pragma unroll
-        for (int k = 9; k < 13; ++k) {
-            const float2 v = dec_tcode2(w[k][0]);
-            a[k] = v.x;
-            b[k] = v.y;
-        }
-        collide_interior<ST::kLog2S, true>(a, ((por >> (2 * q)) & 1u) != 0, d);
-        collide_interior<ST::kLog2S, true>(b, ((por >> (2 * q + 1)) & 1u) != 0, d);
+        for (int k = 9; k < 13; ++k) v[k] = dec_tcode2(w[k][0]);
+        collide_interior2<ST::kLog2S, true>(v, (por >> (2 * q)) & 3u, d);
         uint32_t o[13];
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
             const int dst = PAR == 0 ? (k < 9 ? opp(k) : 8 + opp(k - 8)) : k;
-            o[dst] = k < 9 ? ST::encf2_raw(a[k], b[k]) : enc_tcode2(a[k], b[k]);
+            o[dst] = k < 9 ? ST::encf2_raw(v[k].x, v[k].y) : enc_tcode2(v[k].x, v[k].y);
         }
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
@@ -1623,8 +1707,12 @@ __global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<
     // now; its blocks wait below until this grid has completed
     grid_dependents_go();
     int cur = -1;  // instance whose descriptor sd holds
+    // on a grid-stride launch the next tile's entry is read while this tile
+    // runs, so that a block's tiles follow each other without a wait
+    int4 te_next = blockIdx.x < ntiles ? tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 te = tiles[t];
+        const int4 te = te_next;
+        if (t + (int)gridDim.x < ntiles) te_next = tiles[t + gridDim.x];
         // te.x is the same for the whole block, so the barriers are taken by
         // all of its threads or by none; an observing step also reuses red
         // per tile, so it always synchronises

@@ -409,7 +409,7 @@ static void derive_code_units(InstDesc& h) {
     h.gbc = (float)((double)h.pf.g_beta * (double)h.Tstep);
     h.dT0c = (float)((double)h.pf.dT0 * (double)h.Tscale);
     h.Trefc = (float)((double)h.pf.Tref * (double)h.Tscale);
-    h.pad2 = 0.0f;
+    h.rden = (float)(1.0 / h.pd.den);
 }
 
 static lbm_status upload_desc(lbm_domain* d) {

@@ -103,9 +103,9 @@ struct InstDesc {
     float Tstep, Tscale;
     // the same run's constants for the 16-bit vector path, whose collision
     // takes the heat deviations in code units (value * Tscale): g beta Tstep,
-    // (T0 - Tref) Tscale and Tref Tscale (set from the fields above whenever
-    // the descriptor is uploaded)
-    float gbc, dT0c, Trefc, pad2;
+    // (T0 - Tref) Tscale and Tref Tscale, and 1 / den of the Darcy drag (set
+    // from the fields above whenever the descriptor is uploaded)
+    float gbc, dT0c, Trefc, rden;
 };
 // most blocks that fold one instance's tile partials
 constexpr int FOLD_MAX = 32;
