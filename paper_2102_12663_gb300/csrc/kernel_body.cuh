@@ -796,9 +796,12 @@ __device__ __forceinline__ void collide_interior2(float2* f, uint32_t por, const
 // Collision of a cell pair (cells x and x+1, 13 values each) and its AA-pattern
 // stores; every lane of the warp takes part (odd steps assemble x-shifted
 // links by shuffles).
-template <class ST, int PAR>
+template <class ST, int PAR, bool MASK = false>
 __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int y, float* a,
-                                                   float* b, bool por0, bool por1) {
+                                                   float* b, bool por0, bool por1, bool mine_in = true) {
+    // MASK: some lanes' pairs are not interior (their stores are left out);
+    // else every lane stores (the code of the unmasked pair path)
+    const bool mine = MASK ? mine_in : true;
     using T = typename ST::T;
     const int nx = d.nx, ny = d.ny;
     const int np = (int)d.npad;
@@ -809,17 +812,38 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
     const int rowd = (y == 0 ? ny - 1 : y - 1) * nx;
     const int xl = x == 0 ? nx - 1 : x - 1;
     const int xr = x + 2 == nx ? 0 : x + 2;
-    collide_interior(a, por0, d);
-    collide_interior(b, por1, d);
+    if constexpr (sizeof(T) == 2) {
+        // 16-bit storages: the paired collision (the FP32 kernel measured
+        // faster with the scalar one)
+        float2 v[13];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) v[k] = make_float2(a[k], b[k]);
+        collide_interior2<0, false>(v, (por0 ? 1u : 0u) | (por1 ? 2u : 0u), d);
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            a[k] = v[k].x;
+            b[k] = v[k].y;
+        }
+    } else {
+        collide_interior(a, por0, d);
+        collide_interior(b, por1, d);
+    }
 
     // ---- store --------------------------------------------------------------
+    // Only the results of cells whose pair is interior (mine) are stored; a
+    // store that combines this lane's cell with the neighbouring lane's
+    // (odd steps, x-shifted links) writes each half only for its own pair.
     if (PAR == 0) {
+        if (mine) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
+            for (int q = 0; q < 9; ++q) ST::stf2(P + opp(q) * np + row + x, a[q], b[q], d);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+            for (int i = 1; i <= 4; ++i) ST::stT2(P + (8 + opp(i)) * np + row + x, a[8 + i], b[8 + i], d);
+        }
     } else {
-        ST::stf2(P + row + x, a[0], b[0], d);
+        const bool left_ok = (MASK ? __shfl_up_sync(0xffffffffu, mine, 1) != 0 : true) && lane != 0;
+        const bool right_ok = (MASK ? __shfl_down_sync(0xffffffffu, mine, 1) != 0 : true) && lane != 31;
+        if (mine) ST::stf2(P + row + x, a[0], b[0], d);
 #pragma unroll
         for (int k = 1; k < 13; ++k) {
             const bool heat = k > 8;
@@ -828,31 +852,45 @@ __device__ __forceinline__ void pair_collide_store(const InstDesc& d, int x, int
             const int dr = ey(i) == 1 ? rowu : (ey(i) == -1 ? rowd : row);
             T* dst = P + pl * np + dr;
             if (ex(i) == 0) {
-                if (heat) ST::stT2(dst + x, a[k], b[k], d);
-                else ST::stf2(dst + x, a[k], b[k], d);
+                if (mine) {
+                    if (heat) ST::stT2(dst + x, a[k], b[k], d);
+                    else ST::stf2(dst + x, a[k], b[k], d);
+                }
             } else if (ex(i) == 1) {  // destination columns x+1, x+2
                 const float left = __shfl_up_sync(0xffffffffu, b[k], 1);
-                if (lane != 0) {
+                if (mine && left_ok) {
                     if (heat) ST::stT2(dst + x, left, a[k], d);
                     else ST::stf2(dst + x, left, a[k], d);
                 } else {
-                    if (heat) ST::stT(dst + x + 1, a[k], d);
-                    else ST::stf(dst + x + 1, a[k], d);
+                    if (mine) {
+                        if (heat) ST::stT(dst + x + 1, a[k], d);
+                        else ST::stf(dst + x + 1, a[k], d);
+                    }
+                    if (left_ok) {
+                        if (heat) ST::stT(dst + x, left, d);
+                        else ST::stf(dst + x, left, d);
+                    }
                 }
-                if (lane == 31) {
+                if (lane == 31 && mine) {
                     if (heat) ST::stT(dst + xr, b[k], d);
                     else ST::stf(dst + xr, b[k], d);
                 }
             } else {                  // destination columns x-1, x
                 const float right = __shfl_down_sync(0xffffffffu, a[k], 1);
-                if (lane != 31) {
+                if (mine && right_ok) {
                     if (heat) ST::stT2(dst + x, b[k], right, d);
                     else ST::stf2(dst + x, b[k], right, d);
                 } else {
-                    if (heat) ST::stT(dst + x, b[k], d);
-                    else ST::stf(dst + x, b[k], d);
+                    if (mine) {
+                        if (heat) ST::stT(dst + x, b[k], d);
+                        else ST::stf(dst + x, b[k], d);
+                    }
+                    if (right_ok) {
+                        if (heat) ST::stT(dst + x + 1, right, d);
+                        else ST::stf(dst + x + 1, right, d);
+                    }
                 }
-                if (lane == 0) {
+                if (lane == 0 && mine) {
                     if (heat) ST::stT(dst + xl, a[k], d);
                     else ST::stf(dst + xl, a[k], d);
                 }
@@ -926,10 +964,10 @@ __device__ __forceinline__ void pair_observe(const InstDesc& d, int x, int y, co
     }
 }
 
-template <class ST, int PAR, bool OBS = false, class A = double>
+template <class ST, int PAR, bool OBS = false, class A = double, bool MASK = false>
 __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, int y, bool por0,
                                                      bool por1, uint32_t m2 = 0, int mode = 0,
-                                                     A* acc = nullptr) {
+                                                     A* acc = nullptr, bool mine = true) {
     using T = typename ST::T;
     const int nx = d.nx, ny = d.ny;
     const int np = (int)d.npad;
@@ -987,8 +1025,10 @@ __device__ __forceinline__ void update_pair_interior(const InstDesc& d, int x, i
         }
     }
 
-    if constexpr (OBS) pair_observe<ST, A>(d, x, y, a, b, m2, mode, acc);
-    pair_collide_store<ST, PAR>(d, x, y, a, b, por0, por1);
+    if constexpr (OBS) {
+        if (!MASK || mine) pair_observe<ST, A>(d, x, y, a, b, m2, mode, acc);
+    }
+    pair_collide_store<ST, PAR, MASK>(d, x, y, a, b, por0, por1, mine);
 }
 
 // ---------------------------------------------------------------------------
@@ -1164,12 +1204,35 @@ __device__ __forceinline__ void update_vec16_interior(const InstDesc& d, int x0,
     }
 }
 
-// One row of cell pairs (x, x + 1) of a warp that covers 64 consecutive
-// cells: the pair path where the whole warp's cells are interior, else the
-// general per-cell update.
-template <class ST, bool OBS, int PAR, class A>
+// The masked pair row is rare (rows next to a boundary) and is called out of
+// line: its registers are then allocated apart from the interior pair path's.
+template <class ST, int PAR, bool OBS, class A>
+__device__ __noinline__ void pair_row_masked(const InstDesc& sd, int x, int y, bool por0, bool por1, uint32_t m2,
+                                             int mode, A* acc, bool mine) {
+    update_pair_interior<ST, PAR, OBS, A, true>(sd, x, y, por0, por1, m2, mode, acc, mine);
+}
+
+// The per-cell update of a pair of a plain step's row without the pair path
+// (rare: grids of odd width, tiles 32 wide), out of line.
+template <class ST, int PAR>
+__device__ __noinline__ void cell_pair_slow(const InstDesc& sd, int x, int y) {
+    if (x < sd.nx && y < sd.ny) update_cell<ST, false, PAR, double>(sd, x, y, 0, nullptr);
+    if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, false, PAR, double>(sd, x + 1, y, 0, nullptr);
+}
+
+// One row of cell pairs (x, x + 1) of a warp that covers a 64-cell segment.
+// With the pair path (vec_ok), a segment whose pairs are all interior (both
+// cells fluid or porous, not next to a boundary) takes it.  Otherwise:
+// - an instance that takes edge-cell chunks (SPLIT kernels, sd.split): the
+//   interior pairs of a segment that lies wholly in the grid take the pair
+//   path, the warp's other lanes taking part in its loads and shuffles but
+//   storing nothing; its other cells are edge cells, updated elsewhere;
+// - else every cell of the segment takes the per-cell update.
+template <class ST, bool OBS, int PAR, class A, bool SPLIT>
 __device__ __forceinline__ void pair_row(const InstDesc& sd, int x, int y, bool pure, bool vec_ok, int mode,
                                          A* acc) {
+    bool split = SPLIT;
+    if constexpr (SPLIT && sizeof(typename ST::T) == 4) split = sd.split != 0;
     bool fast = false;
     if (vec_ok) {
         uint32_t m2 = 0u;
@@ -1180,19 +1243,58 @@ __device__ __forceinline__ void pair_row(const InstDesc& sd, int x, int y, bool 
             if (in) m2 = *reinterpret_cast<const uint16_t*>(sd.mask + (int64_t)y * sd.nx + x);
             else m2 = 0xFFFFu;
             // both cells fluid or porous (type bits 1-2 clear) and not next to a boundary (bit 3)
-            fast = __all_sync(0xffffffffu, (m2 & 0x0E0Eu) == 0u);
+            const bool mine = (m2 & 0x0E0Eu) == 0u;
+            fast = __all_sync(0xffffffffu, mine);
+            if constexpr (SPLIT) {
+                // every lane in the grid: the segment lies wholly in it
+                if (!fast && split && __all_sync(0xffffffffu, in) && __any_sync(0xffffffffu, mine))
+                    pair_row_masked<ST, PAR, OBS, A>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
+                                                     (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode, acc, mine);
+            }
         }
         if (fast)
             update_pair_interior<ST, PAR, OBS, A>(sd, x, y, (m2 & 1u) != 0 && sd.tm_model == 0,
-                                               (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode, acc);
+                                                  (m2 & 0x100u) != 0 && sd.tm_model == 0, m2, mode, acc);
     }
-    if (!fast) {
-        if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
-        if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x + 1, y, mode, acc);
+    if (!fast && !(split && vec_ok)) {
+        if constexpr (SPLIT) {
+            cell_pair_slow<ST, PAR>(sd, x, y);
+        } else {
+            if (x < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x, y, mode, acc);
+            if (x + 1 < sd.nx && y < sd.ny) update_cell<ST, OBS, PAR, A>(sd, x + 1, y, mode, acc);
+        }
     }
 }
 
-template <class ST, bool OBS, int PAR, class A = double>
+// The edge cells of one tile (the dataflow kernel, after the tile's rows):
+// one per thread of the block, through the per-cell update.  Out of line, so
+// that its registers are allocated apart from the rows'.
+template <class ST, int PAR>
+__device__ __noinline__ void tile_edge_cells(const InstDesc& sd, int li) {
+    if (li < 0 || li >= sd.ntiles) return;  // not a tile of this instance
+    const int e1 = sd.eoff[li + 1];
+    const int nthreads = blockDim.x * blockDim.y;
+    for (int e = sd.eoff[li] + (int)(threadIdx.y * blockDim.x + threadIdx.x); e < e1; e += nthreads) {
+        const int c = sd.edges[e];
+        const int y = c / sd.nx;
+        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr);
+    }
+}
+
+// An edge-cell chunk {instance, TILE_EDGE, first, count}: one edge cell per
+// thread of the block, through the per-cell update (a plain step).
+template <class ST, int PAR>
+__device__ __noinline__ void edge_block(const InstDesc& sd, int4 te) {
+    const int k = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+    if (k < te.w) {
+        const int c = sd.edges[te.z + k];
+        const int y = c / sd.nx;
+        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr);
+    }
+}
+
+// SPLIT: a plain step whose edge cells come in chunks of their own (pair_row)
+template <class ST, bool OBS, int PAR, class A = double, bool SPLIT = false>
 __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, int mode, const Shape& shape,
                                           A* acc) {
     const int rpt = shape.rpt;
@@ -1241,14 +1343,14 @@ __device__ __forceinline__ void tile_rows(const InstDesc& sd, const int4& te, in
                 if (!fast) {
 #pragma unroll 1
                     for (int s = 0; s < V16 / 2; ++s)
-                        pair_row<ST, OBS, PAR, A>(sd, te.z + 64 * s + 2 * (int)threadIdx.x, y, pure, vec_ok, mode, acc);
+                        pair_row<ST, OBS, PAR, A, SPLIT>(sd, te.z + 64 * s + 2 * (int)threadIdx.x, y, pure, vec_ok, mode, acc);
                 }
             }
         } else {
             const int x = te.z + 2 * threadIdx.x;
             for (int r = 0; r < rpt; ++r) {
                 const int y = te.w + threadIdx.y + r * blockDim.y;
-                pair_row<ST, OBS, PAR, A>(sd, x, y, pure, vec_ok, mode, acc);
+                pair_row<ST, OBS, PAR, A, SPLIT>(sd, x, y, pure, vec_ok, mode, acc);
             }
         }
     } else {
@@ -1695,7 +1797,9 @@ __global__ void __launch_bounds__(WS_THREADS, LBM_WS_MINB) step_kernel_ws(const 
 // check step (which also writes).
 // MB > 0: resident blocks of 256 threads to compile for (a register budget
 // chosen per launch geometry), else the storage's default
-template <class ST, bool OBS, class A = double, int MB = 0>
+// SPLIT (plain FP32-arithmetic steps): the launch runs the edge-cell chunks
+// that lead the tile list, and the rows update interior pairs only
+template <class ST, bool OBS, class A = double, int MB = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<ST>())) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int flip, int mode, Shape shape) {
@@ -1728,11 +1832,19 @@ __global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<
         // completed and its writes are visible before any population is touched
         grid_dependency_wait();
         const int parity = (sd.parity ^ flip) & 1;
+        constexpr bool split = SPLIT && !OBS && sizeof(typename ST::R) == 4;
+        if constexpr (split) {
+            if (te.y & TILE_EDGE) {
+                if (parity) edge_block<ST, 1>(sd, te);
+                else edge_block<ST, 0>(sd, te);
+                continue;
+            }
+        }
         A acc[NPART];
 #pragma unroll
         for (int k = 0; k < NPART; ++k) acc[k] = A(0);
-        if (parity) tile_rows<ST, OBS, 1, A>(sd, te, mode, shape, acc);
-        else tile_rows<ST, OBS, 0, A>(sd, te, mode, shape, acc);
+        if (parity) tile_rows<ST, OBS, 1, A, split>(sd, te, mode, shape, acc);
+        else tile_rows<ST, OBS, 0, A, split>(sd, te, mode, shape, acc);
         if (OBS && (mode & OBS_STATS)) {
             warp_block_reduce<A>(acc, red, sd.partials + (int64_t)(te.y & TILE_INDEX) * NPART);
         }
@@ -1796,7 +1908,9 @@ __device__ __forceinline__ void flow_wait(const int* done, int target, int* flag
     atomicExch(flags, 1);
 }
 
-template <class ST, int MB = 0>
+// SPLIT: the same path for every cell as the SPLIT per-step kernel (interior
+// pairs in the rows, then the tile's own edge cells)
+template <class ST, int MB = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(256, MB > 0 ? MB : flow_min_blocks<ST>())
     step_kernel_flow(const InstDesc* __restrict__ insts, const FlowArgs fa, Shape shape) {
     __shared__ __align__(16) InstDesc sd;
@@ -1827,8 +1941,15 @@ __global__ void __launch_bounds__(256, MB > 0 ? MB : flow_min_blocks<ST>())
         __syncthreads();
         const int parity = (sd.parity ^ fa.flip ^ s) & 1;
         double acc[NPART];
-        if (parity) tile_rows<ST, false, 1>(sd, te, 0, shape, acc);
-        else tile_rows<ST, false, 0>(sd, te, 0, shape, acc);
+        constexpr bool split = SPLIT && sizeof(typename ST::R) == 4;
+        if (parity) tile_rows<ST, false, 1, double, split>(sd, te, 0, shape, acc);
+        else tile_rows<ST, false, 0, double, split>(sd, te, 0, shape, acc);
+        if constexpr (split) {
+            if (sd.split && (blockDim.x & 31) == 0 && (sd.nx & 1) == 0 && !(te.y & TILE_PURE)) {
+                if (parity) tile_edge_cells<ST, 1>(sd, t - sd.tile_base);
+                else tile_edge_cells<ST, 0>(sd, t - sd.tile_base);
+            }
+        }
         __syncthreads();
         // a thread outside warp 0 reports, so that the release overlaps warp
         // 0's polls for the next item

@@ -27,12 +27,25 @@ StepPlan step_plan(int precision, int mode, Shape shape) {
     return precision == 0 ? step_plan_f64(mode, shape) : step_plan_lp(precision, mode, shape);
 }
 
-cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
-                        int flip, int mode, Shape shape, int grid, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
+// The entries a plan's kernel runs: a plain FP32-arithmetic step all of them
+// (the edge-cell chunks first), the other kernels the tiles after the chunks.
+// Its grid: one block per entry, or at most cap blocks (cap > 0) looping over them.
+static void plan_entries(const StepPlan& pl, const int4* all, int nchunks, int ntiles, int cap, const int4** t,
+                         int* n, int* grid) {
+    *t = pl.edges ? all : all + nchunks;
+    *n = pl.edges ? nchunks + ntiles : ntiles;
+    *grid = std::max(1, cap > 0 ? std::min(cap, *n) : *n);
+    if (pl.max_grid > 0) *grid = std::min(*grid, pl.max_grid);
+}
+
+cudaError_t launch_step(int precision, const InstDesc* insts, const int4* all, int nchunks, int ntiles,
+                        int flip, int mode, Shape shape, int cap, cudaStream_t s) {
     const StepPlan pl = step_plan(precision, mode, shape);
-    if (pl.max_grid > 0) grid = std::min(grid, pl.max_grid);
-    void* args[] = {&insts, &tiles, &ntiles, &flip, &mode, &shape};
+    const int4* tiles = nullptr;
+    int n = 0, grid = 0;
+    plan_entries(pl, all, nchunks, ntiles, cap, &tiles, &n, &grid);
+    if (n <= 0) return cudaSuccess;
+    void* args[] = {&insts, &tiles, &n, &flip, &mode, &shape};
     return cudaLaunchKernel(pl.func, dim3(grid), pl.block, args, pl.smem, s);
 }
 
@@ -95,8 +108,9 @@ static size_t store_size(int prec) {
 static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct Layout {
-    int64_t npad, max_tiles;
-    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, fold, total;
+    int64_t npad, max_tiles, max_entries;
+    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, fold, edges, eoff,
+        total;
     int64_t max_curved;
 };
 
@@ -121,7 +135,9 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.desc = off; off = align_up(off + sizeof(InstDesc));
     L.obs = off; off = align_up(off + NOBS * sizeof(double));
     L.mask = off; off = align_up(off + (size_t)L.npad);
-    L.tiles = off; off = align_up(off + (size_t)L.max_tiles * sizeof(int4));
+    // tile list: the edge-cell chunks (at most one per 32 cells) and the tiles
+    L.max_entries = L.max_tiles + L.npad / 32 + 1;
+    L.tiles = off; off = align_up(off + (size_t)L.max_entries * sizeof(int4));
     L.nbr = off; off = align_up(off + (size_t)L.max_tiles * 8 * sizeof(int));
     L.flags = off; off = align_up(off + (size_t)(L.max_tiles + 2) * sizeof(int));
     L.items = off; off = align_up(off + (size_t)SWEEP_MAX * L.max_tiles * sizeof(int4));
@@ -134,6 +150,9 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.pops = off; off = align_up(off + 13 * (size_t)L.npad * ss);
     L.tmap = off; off = align_up(off + sizeof(CUtensorMap));
     L.fold = off; off = align_up(off + ((size_t)FOLD_MAX * NPART + 1) * sizeof(double));
+    // edge cells: at most one entry per cell, and per-tile offsets
+    L.edges = off; off = align_up(off + (size_t)L.npad * sizeof(int32_t));
+    L.eoff = off; off = align_up(off + (size_t)(L.max_tiles + 1) * sizeof(int32_t));
     L.total = off;
     return true;
 }
@@ -169,6 +188,12 @@ struct lbm_domain {
     cudaEvent_t pin_ev[2] = {nullptr, nullptr};
     int ntiles = 0;
     int64_t tiled_cells = 0;
+    int64_t n_edges = 0;              // edge cells (plain FP32-arithmetic steps)
+    int nchunks = 0;                  // edge-cell chunks leading d_tiles
+    int split = 0;                    // plain steps take the edge-cell chunks (Shape::split)
+    int64_t active_cells = 0;         // fluid and porous cells
+    int64_t slow_cells = 0;           // active cells of row segments that need the per-cell update
+    std::vector<int4> hchunks;        // host copy of them (instance 0)
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     lbm_params params{};
     bool have_params = false;
@@ -218,11 +243,19 @@ static bool launch_ok(const lbm_launch& l, int prec) {
 // wavefront lag between consecutive steps of a sweep, in bands (tile rows)
 static constexpr int DEFAULT_SWEEP_LAG = 8;
 
-static Shape shape_of(const lbm_launch& l) { return Shape{l.tile_w, l.block_rows, l.rows_per_thread}; }
+static Shape shape_of(const lbm_launch& l, int split) {
+    return Shape{l.tile_w, l.block_rows, l.rows_per_thread, split};
+}
 
-static int grid_of(const lbm_domain* d, int ntiles) {
-    if (d->launch.blocks_per_sm <= 0) return std::max(ntiles, 1);
-    return std::max(1, std::min(ntiles, d->launch.blocks_per_sm * d->num_sms));
+// FP32 grids take edge-cell chunks (Shape::split) when more than this share
+// of their active cells lie in row segments that would otherwise run the
+// per-cell update (the chunks' own per-cell work and the masked rows cost a
+// few per cent of the interior rows' speed; 16-bit storages always take them)
+constexpr double SPLIT_SHARE = 0.08;
+
+// cap on the blocks of a step launch (0: one block per entry)
+static int grid_cap(const lbm_domain* d) {
+    return d->launch.blocks_per_sm > 0 ? d->launch.blocks_per_sm * d->num_sms : 0;
 }
 
 // Launch order of a domain's per-step kernels.  On a large tile list (many
@@ -271,6 +304,61 @@ static lbm_status build_tiles(lbm_domain* d) {
         }
     }
     if ((int64_t)tiles.size() > d->L.max_tiles) return fail(LBM_EINVAL, "tile list overflow");
+    // Edge cells (FP32-arithmetic kernels whose rows take the pair or vector
+    // path: warps of 32 threads on a row, an even grid width).  A row is taken
+    // in 64-cell segments from the tile's origin; the pair (x, x + 1), x even,
+    // of a segment that lies wholly in the grid is interior when both cells
+    // are fluid or porous and not next to a boundary (the kernels' mask test).
+    // Every other active cell is an edge cell, which a plain step updates in
+    // an edge-cell chunk: one cell per thread of a block.
+    std::vector<int32_t> edges, eoff(tiles.size() + 1, 0);
+    const int cpt = cells_per_thread(d->prec, tw);
+    const bool pair_rows = d->prec != LBM_F64 && (tw / cpt) % 32 == 0 && d->nx % 2 == 0;
+    int64_t active = 0, slow = 0;
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        eoff[k] = (int32_t)edges.size();
+        const int x0 = tiles[k].z, y0 = tiles[k].w;
+        if (tiles[k].y & TILE_PURE) {
+            active += (int64_t)tw * th;
+            continue;
+        }
+        for (int y = y0; y < std::min(d->ny, y0 + th); ++y) {
+            const uint8_t* row = d->hmask.data() + (int64_t)y * d->nx;
+            for (int seg = x0; seg < std::min(d->nx, x0 + tw); seg += 64) {
+                const int end = std::min(std::min(d->nx, seg + 64), x0 + tw);
+                int n_act = 0;
+                bool all_interior = pair_rows && seg + 64 <= d->nx;
+                for (int x = seg; x < end; ++x) {
+                    if ((row[x] & TYPE_BITS) <= POROUS) ++n_act;
+                    if (row[x] & 0x0E) all_interior = false;
+                }
+                active += n_act;
+                if (!all_interior) slow += n_act;
+                if (!pair_rows) continue;
+                for (int x = seg; x < end; ++x) {
+                    if ((row[x] & TYPE_BITS) > POROUS) continue;
+                    const int xp = x & ~1;
+                    const bool interior = seg + 64 <= d->nx && (row[xp] & 0x0E) == 0 && (row[xp + 1] & 0x0E) == 0;
+                    if (!interior) edges.push_back((int32_t)((int64_t)y * d->nx + x));
+                }
+            }
+        }
+    }
+    d->active_cells = active;
+    d->slow_cells = slow;
+    d->split = pair_rows && (d->prec != LBM_F32 || (double)slow > SPLIT_SHARE * (double)std::max<int64_t>(active, 1));
+    d->h.split = d->split;
+    if (!d->split) {  // the rows update every cell: no edge cells
+        edges.clear();
+        std::fill(eoff.begin(), eoff.end(), 0);
+    }
+    eoff[tiles.size()] = (int32_t)edges.size();
+    if ((int64_t)edges.size() > d->L.npad) return fail(LBM_EINVAL, "edge list overflow");
+    const int per_chunk = (tw / cpt) * d->launch.block_rows;  // threads of a block
+    std::vector<int4> chunks;
+    for (size_t e = 0; e < edges.size(); e += (size_t)per_chunk)
+        chunks.push_back(make_int4(0, TILE_EDGE, (int)e, (int)std::min<size_t>(per_chunk, edges.size() - e)));
+    if ((int64_t)(chunks.size() + tiles.size()) > d->L.max_entries) return fail(LBM_EINVAL, "tile list overflow");
     // neighbour tiles in the order of the links e_1..e_8, wrapping around
     // periodic edges only (no active cell lies on a non-periodic edge, so no
     // link crosses one)
@@ -313,7 +401,11 @@ static lbm_status build_tiles(lbm_domain* d) {
     d->tiled_cells = cells;
     d->h.ntiles = d->ntiles;
     d->htiles = tiles;
-    const std::vector<int4> launch_order = boundary_tiles_first(tiles);
+    // per-step launch order: the edge-cell chunks, then the tiles, boundary
+    // tiles first (the longer blocks start early)
+    std::vector<int4> launch_order = chunks;
+    const std::vector<int4> tile_order = boundary_tiles_first(tiles);
+    launch_order.insert(launch_order.end(), tile_order.begin(), tile_order.end());
     if (!tiles.empty()) {
         CK(cudaMemcpyAsync(d->d_tiles, launch_order.data(), launch_order.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, d->stream));
@@ -322,10 +414,18 @@ static lbm_status build_tiles(lbm_domain* d) {
         CK(cudaMemcpyAsync(d->d_items, items.data(), items.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, d->stream));
     }
+    CK(cudaMemcpyAsync(d->base + d->L.eoff, eoff.data(), eoff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       d->stream));
+    if (!edges.empty())
+        CK(cudaMemcpyAsync(d->base + d->L.edges, edges.data(), edges.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, d->stream));
+    d->n_edges = (int64_t)edges.size();
+    d->nchunks = (int)chunks.size();
+    d->hchunks = chunks;
     // co-resident blocks of the dataflow kernel for this shape
     d->flow_grid = 0;
     if (d->coop) {
-        const StepPlan pl = flow_plan(d->prec, shape_of(d->launch), d->sweep_k > 1);
+        const StepPlan pl = flow_plan(d->prec, shape_of(d->launch, d->split), d->sweep_k > 1);
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.func,
                                                          (int)(pl.block.x * pl.block.y), pl.smem));
@@ -822,6 +922,8 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     h.mask = reinterpret_cast<const uint8_t*>(d->base + d->L.mask);
     h.usnap = d->base + d->L.usnap;
     h.partials = reinterpret_cast<double*>(d->base + d->L.partials);
+    h.edges = reinterpret_cast<const int32_t*>(d->base + d->L.edges);
+    h.eoff = reinterpret_cast<const int32_t*>(d->base + d->L.eoff);
     h.obs = d->d_obs;
     h.npad = d->L.npad;
     h.nx = d->nx;
@@ -1045,8 +1147,8 @@ extern "C" lbm_status lbm_reset_state(lbm_domain* d) {
 // stepping
 
 static lbm_status step_once(lbm_domain* d, int mode) {
-    CK(launch_step(d->prec, d->d_desc, d->d_tiles, d->ntiles, (int)(d->step & 1), mode,
-                   shape_of(d->launch), grid_of(d, d->ntiles), d->stream));
+    CK(launch_step(d->prec, d->d_desc, d->d_tiles, d->nchunks, d->ntiles, (int)(d->step & 1), mode,
+                   shape_of(d->launch, d->split), grid_cap(d), d->stream));
     if (mode == 0 || (mode & OBS_WRITE)) d->step += 1;
     return LBM_OK;
 }
@@ -1060,8 +1162,8 @@ static lbm_status step_once(lbm_domain* d, int mode) {
 // visible, so the launch latency and block ramp-up of each step overlap the
 // previous step's tail.  Falls back to plain dependencies where that is not
 // available.
-static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int4* tiles,
-                                      int ntiles, Shape sh, int grid, int nsteps, bool pdl,
+static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int4* all, int nchunks,
+                                      int ntiles, Shape sh, int cap, int nsteps, bool pdl,
                                       cudaGraphExec_t* out) {
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -1072,11 +1174,13 @@ static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int
         return e;
     }
     const StepPlan pl = step_plan(prec, 0, sh);
-    const int gsz = pl.max_grid > 0 ? std::min(grid, pl.max_grid) : grid;
+    const int4* tiles = nullptr;
+    int n = 0, gsz = 0;
+    plan_entries(pl, all, nchunks, ntiles, cap, &tiles, &n, &gsz);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         const InstDesc* a0 = insts;
         const int4* a1 = tiles;
-        int a2 = ntiles, a3 = k & 1, a4 = 0;
+        int a2 = n, a3 = k & 1, a4 = 0;
         Shape a5 = sh;
         void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
         cudaLaunchAttribute attr[1];
@@ -1100,21 +1204,21 @@ static cudaError_t capture_step_graph(int prec, const InstDesc* insts, const int
     return e;
 }
 
-static cudaError_t step_graph(int prec, const InstDesc* insts, const int4* tiles, int ntiles,
-                              Shape sh, int grid, int nsteps, cudaGraphExec_t* out) {
+static cudaError_t step_graph(int prec, const InstDesc* insts, const int4* all, int nchunks, int ntiles,
+                              Shape sh, int cap, int nsteps, cudaGraphExec_t* out) {
     *out = nullptr;
-    cudaError_t e = capture_step_graph(prec, insts, tiles, ntiles, sh, grid, nsteps, true, out);
+    cudaError_t e = capture_step_graph(prec, insts, all, nchunks, ntiles, sh, cap, nsteps, true, out);
     if (e == cudaSuccess) return e;
     (void)cudaGetLastError();  // clear the failed attempt
     *out = nullptr;
-    return capture_step_graph(prec, insts, tiles, ntiles, sh, grid, nsteps, false, out);
+    return capture_step_graph(prec, insts, all, nchunks, ntiles, sh, cap, nsteps, false, out);
 }
 
 // GRAPH_STEPS plain steps from an even step, replayed by lbm_step
 static lbm_status ensure_graph(lbm_domain* d) {
     if (d->graph) return LBM_OK;
-    const cudaError_t e = step_graph(d->prec, d->d_desc, d->d_tiles, d->ntiles, shape_of(d->launch),
-                                     grid_of(d, d->ntiles), GRAPH_STEPS, &d->graph);
+    const cudaError_t e = step_graph(d->prec, d->d_desc, d->d_tiles, d->nchunks, d->ntiles, shape_of(d->launch, d->split),
+                                     grid_cap(d), GRAPH_STEPS, &d->graph);
     if (e != cudaSuccess) {
         d->graph = nullptr;
         return fail(LBM_ECUDA, "graph construction failed: %s", cudaGetErrorString(e));
@@ -1135,7 +1239,7 @@ extern "C" lbm_status lbm_step(lbm_domain* d, int64_t nsteps) {
             const int n = (int)std::min<int64_t>(nsteps - k, chunk);
             FlowArgs fa{d->d_items, d->d_nbr, d->d_flags, d->ntiles, d->per_sweep, d->sweep_k, n,
                         (int)(d->step & 1), d->stall_tile};
-            CK(launch_flow(d->prec, d->d_desc, fa, shape_of(d->launch), d->sweep_k > 1,
+            CK(launch_flow(d->prec, d->d_desc, fa, shape_of(d->launch, d->split), d->sweep_k > 1,
                            d->flow_grid, d->stream));
             d->step += n;
             k += n;
@@ -1575,6 +1679,8 @@ struct lbm_batch {
     std::vector<double> hobs;
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     int ntiles = 0;
+    int nchunks = 0;  // edge-cell chunks leading d_tiles
+    int split = 0;    // plain steps take the edge-cell chunks (Shape::split)
     bool dirty = true;
     // per-step launches take the tiles holding boundary cells (the slower
     // general update) first, then the pure tiles; the autotuner tries both
@@ -1591,7 +1697,8 @@ static BatchLayout batch_layout(int max_inst, int64_t max_tiles) {
     size_t off = 0;
     L.table = off; off = align_up(off + (size_t)max_inst * sizeof(InstDesc));
     L.obs = off; off = align_up(off + (size_t)max_inst * NOBS * sizeof(double));
-    L.tiles = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
+    // per-step list: the tiles and up to as many edge-cell chunks
+    L.tiles = off; off = align_up(off + (size_t)2 * max_tiles * sizeof(int4));
     L.nbr = off; off = align_up(off + (size_t)max_tiles * 8 * sizeof(int));
     L.flags = off; off = align_up(off + (size_t)(max_tiles + 2) * sizeof(int));
     L.items = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
@@ -1690,10 +1797,11 @@ extern "C" int32_t lbm_batch_size(const lbm_batch* b) { return b ? (int32_t)b->m
 // one work item per tile (batch index | TILE_PURE)
 static lbm_status batch_rebuild(lbm_batch* b) {
     if (!b->dirty) return LBM_OK;
-    std::vector<int4> tiles, items;
+    std::vector<int4> tiles, items, chunks;
     std::vector<int> nbr;
     for (size_t k = 0; k < b->members.size(); ++k) {
         const lbm_domain* m = b->members[k];
+        for (const int4& c : m->hchunks) chunks.push_back(make_int4((int)k, c.y, c.z, c.w));
         const int base = (int)tiles.size();
         for (size_t j = 0; j < m->htiles.size(); ++j) {
             const int4& t = m->htiles[j];
@@ -1710,8 +1818,17 @@ static lbm_status batch_rebuild(lbm_batch* b) {
     if (b->boundary_first) {  // per-step order only: the dataflow items keep their wavefront order
         std::stable_partition(tiles.begin(), tiles.end(), [](const int4& t) { return !(t.y & TILE_PURE); });
     }
+    // the split kernels when any member takes edge-cell chunks (each member
+    // keeps its own choice, so it computes the same alone and in the batch)
+    b->split = 0;
+    for (const lbm_domain* m : b->members) b->split |= m->split;
+    if ((int64_t)(chunks.size() + tiles.size()) > 2 * b->max_tiles)
+        return fail(LBM_EBUSY, "batch tile capacity exceeded (edge-cell chunks)");
+    // per-step list: the members' edge-cell chunks, then the tiles
+    std::vector<int4> order = chunks;
+    order.insert(order.end(), tiles.begin(), tiles.end());
     if (!tiles.empty()) {
-        CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(b->d_tiles, order.data(), order.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            b->stream));
         CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, b->stream));
@@ -1720,7 +1837,7 @@ static lbm_status batch_rebuild(lbm_batch* b) {
     }
     b->flow_grid = 0;
     if (b->coop) {
-        const StepPlan pl = flow_plan(b->prec, shape_of(b->launch), false);
+        const StepPlan pl = flow_plan(b->prec, shape_of(b->launch, b->split), false);
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.func,
                                                          (int)(pl.block.x * pl.block.y), pl.smem));
@@ -1729,6 +1846,8 @@ static lbm_status batch_rebuild(lbm_batch* b) {
     }
     CK(cudaStreamSynchronize(b->stream));
     b->ntiles = (int)tiles.size();
+    b->nchunks = (int)chunks.size();
+
     batch_drop_graph(b);
     b->dirty = false;
     return LBM_OK;
@@ -1738,9 +1857,12 @@ static lbm_status batch_rebuild(lbm_batch* b) {
 // slot of the batch's contiguous observables array
 static lbm_status batch_upload_table(lbm_batch* b) {
     b->htable.resize(b->members.size());
+    int32_t base = 0;  // the member's first tile in the merged list (batch_rebuild's order)
     for (size_t k = 0; k < b->members.size(); ++k) {
         InstDesc t = b->members[k]->h;
         derive_code_units(t);
+        t.tile_base = base;
+        base += b->members[k]->ntiles;
         t.parity = (int)(b->members[k]->step & 1);
         t.obs = b->d_obs + k * NOBS;
         b->htable[k] = t;
@@ -1751,15 +1873,14 @@ static lbm_status batch_upload_table(lbm_batch* b) {
     return LBM_OK;
 }
 
-static int batch_grid(const lbm_batch* b) {
-    if (b->launch.blocks_per_sm <= 0) return std::max(b->ntiles, 1);
-    return std::max(1, std::min(b->ntiles, b->launch.blocks_per_sm * b->num_sms));
+static int batch_cap(const lbm_batch* b) {
+    return b->launch.blocks_per_sm > 0 ? b->launch.blocks_per_sm * b->num_sms : 0;
 }
 
 static lbm_status batch_ensure_graph(lbm_batch* b) {
     if (b->graph) return LBM_OK;
-    const cudaError_t e = step_graph(b->prec, b->d_table, b->d_tiles, b->ntiles, shape_of(b->launch),
-                                     batch_grid(b), BATCH_GRAPH_STEPS, &b->graph);
+    const cudaError_t e = step_graph(b->prec, b->d_table, b->d_tiles, b->nchunks, b->ntiles, shape_of(b->launch, b->split),
+                                     batch_cap(b), BATCH_GRAPH_STEPS, &b->graph);
     if (e != cudaSuccess) {
         b->graph = nullptr;
         return fail(LBM_ECUDA, "batch graph construction failed: %s", cudaGetErrorString(e));
@@ -1781,7 +1902,7 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
         while (k < nsteps) {
             const int n = (int)std::min<int64_t>(nsteps - k, chunk);
             FlowArgs fa{b->d_items, b->d_nbr, b->d_flags, b->ntiles, b->ntiles, 1, n, 0, -1};
-            CK(launch_flow(b->prec, b->d_table, fa, shape_of(b->launch), false, b->flow_grid,
+            CK(launch_flow(b->prec, b->d_table, fa, shape_of(b->launch, b->split), false, b->flow_grid,
                            b->stream));
             k += n;
         }
@@ -1792,8 +1913,8 @@ extern "C" lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
             CK(cudaGraphLaunch(b->graph, b->stream));
     }
     for (; k < nsteps; ++k)
-        CK(launch_step(b->prec, b->d_table, b->d_tiles, b->ntiles, (int)(k & 1), 0,
-                       shape_of(b->launch), batch_grid(b), b->stream));
+        CK(launch_step(b->prec, b->d_table, b->d_tiles, b->nchunks, b->ntiles, (int)(k & 1), 0,
+                       shape_of(b->launch, b->split), batch_cap(b), b->stream));
     for (lbm_domain* m : b->members) m->step += nsteps;
     return LBM_OK;
 }
@@ -1805,8 +1926,8 @@ extern "C" lbm_status lbm_batch_check(lbm_batch* b, int32_t check_every) {
     lbm_status st;
     if ((st = lbm_batch_step(b, check_every - 1)) != LBM_OK) return st;
     if ((st = batch_rebuild(b)) != LBM_OK || (st = batch_upload_table(b)) != LBM_OK) return st;
-    CK(launch_step(b->prec, b->d_table, b->d_tiles, b->ntiles, 0,
-                   OBS_STATS | OBS_SNAP | OBS_WRITE | OBS_RESID, shape_of(b->launch), batch_grid(b),
+    CK(launch_step(b->prec, b->d_table, b->d_tiles, b->nchunks, b->ntiles, 0,
+                   OBS_STATS | OBS_SNAP | OBS_WRITE | OBS_RESID, shape_of(b->launch, b->split), batch_cap(b),
                    b->stream));
     for (lbm_domain* m : b->members) m->step += 1;
     const int n = (int)b->members.size();

@@ -106,6 +106,21 @@ struct InstDesc {
     // (T0 - Tref) Tscale and Tref Tscale, and 1 / den of the Darcy drag (set
     // from the fields above whenever the descriptor is uploaded)
     float gbc, dT0c, Trefc, rden;
+    // Edge cells of the FP32-arithmetic plain steps (cell indices y nx + x):
+    // the active cells that no interior cell pair of the pair or vector path
+    // covers, in tile order, those of local tile t at edges[eoff[t] ..
+    // eoff[t + 1]).  Per-step launches hand them out in entries of the tile
+    // list flagged TILE_EDGE (one cell per thread of a block); the dataflow
+    // kernel updates a tile's own after its rows.
+    const int32_t* edges;
+    const int32_t* eoff;
+    // first tile of this instance in a batch's merged tile list (0 for a
+    // domain): the dataflow items carry merged indices, eoff local ones
+    int32_t tile_base;
+    // this instance's plain steps take its edge-cell chunks (FP32: the
+    // host's choice for the grid; always for the 16-bit storages); else its
+    // rows update every cell and it has no edge cells
+    int32_t split;
 };
 // most blocks that fold one instance's tile partials
 constexpr int FOLD_MAX = 32;
@@ -123,10 +138,19 @@ __host__ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDes
 // fluid cells none of which links to a boundary: the FP32-arithmetic kernels
 // update it by the pair path without reading its mask.
 constexpr int TILE_PURE = 1 << 30;
-constexpr int TILE_INDEX = TILE_PURE - 1;
+// an edge-cell chunk {instance, TILE_EDGE, first, count}: cells edges[first ..
+// first + count) of the instance, one per thread, in plain steps of the
+// FP32-arithmetic kernels (the chunks lead the tile list; the other kernels
+// are launched on the tiles after them)
+constexpr int TILE_EDGE = 1 << 29;
+constexpr int TILE_INDEX = TILE_EDGE - 1;
 
 struct Shape {
     int tw, bh, rpt;  // tile = tw x (bh * rpt) cells, block = (tw / V) x bh threads
+    // plain FP32-arithmetic steps with edge-cell chunks (the host's choice
+    // for the grid: every 16-bit storage, FP32 grids with many cells in row
+    // segments next to a boundary); 0: the rows update every cell
+    int split = 0;
 };
 
 // Cells per thread along x: the FP32-arithmetic kernels take cell pairs
@@ -383,8 +407,9 @@ using StBF16 = StBF16T<ST_STREAM>;
 
 // ---- launchers (one translation unit per arithmetic precision) -----------
 // precision: 0 f64, 1 f32, 2 f16-dev, 3 bf16-dev.
-cudaError_t launch_step(int precision, const InstDesc* insts, const int4* tiles, int ntiles,
-                        int flip, int mode, Shape shape, int grid, cudaStream_t s);
+// all: nchunks edge-cell chunks, then ntiles tiles; cap: most blocks (0: one per entry)
+cudaError_t launch_step(int precision, const InstDesc* insts, const int4* all, int nchunks, int ntiles,
+                        int flip, int mode, Shape shape, int cap, cudaStream_t s);
 cudaError_t launch_finalize(const InstDesc* insts, int ninst, cudaStream_t s);
 
 // Kernel, block shape and dynamic shared memory of one step launch (also the
@@ -394,6 +419,7 @@ struct StepPlan {
     dim3 block;
     size_t smem;
     int max_grid = 0;  // persistent kernels: co-resident blocks on the device (0: no cap)
+    bool edges = false;  // runs the edge-cell chunks that lead the tile list
 };
 // mode: the step's observation mode (0 for a plain step)
 StepPlan step_plan(int precision, int mode, Shape shape);

@@ -46,15 +46,25 @@ static StepPlan plan_t(int mode, Shape shape) {
         // planes of four packed words live and is built for 2 blocks of 256
         // threads (128 registers); the other shapes for 3 (85 registers: more
         // warps to hide memory latency)
-        const void* plain = reinterpret_cast<const void*>(&step_kernel<ST, false>);
-        if (sizeof(typename ST::T) == 2)
-            plain = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel<ST, false, double, 2>)
-                                    : reinterpret_cast<const void*>(&step_kernel<ST, false, double, 3>);
+        // Plain steps: the 16-bit storages always with edge-cell chunks (their
+        // vector rows would otherwise send up to 256 cells to the per-cell
+        // update for one boundary cell); FP32 as the host chose for the grid
+        const void* plain = nullptr;
+        bool split = true;
+        if constexpr (sizeof(typename ST::T) == 2) {
+            plain = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel<ST, false, double, 2, true>)
+                                    : reinterpret_cast<const void*>(&step_kernel<ST, false, double, 3, true>);
+        } else {
+            split = shape.split != 0;
+            plain = split ? reinterpret_cast<const void*>(&step_kernel<ST, false, double, 0, true>)
+                          : reinterpret_cast<const void*>(&step_kernel<ST, false>);
+        }
         p.func = !obs ? plain
                  : (mode & OBS_WRITE) ? reinterpret_cast<const void*>(&step_kernel<ST, true, typename ST::A>)
                                       : reinterpret_cast<const void*>(&step_kernel<ST, true>);
         p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
         p.smem = 0;
+        p.edges = !obs && split;  // runs the edge-cell chunks
     }
     return p;
 }
@@ -70,10 +80,14 @@ StepPlan step_plan_lp(int precision, int mode, Shape shape) {
 template <class ST>
 static StepPlan flow_t(Shape shape) {
     StepPlan p;
-    p.func = reinterpret_cast<const void*>(&step_kernel_flow<ST>);
-    if (sizeof(typename ST::T) == 2)
-        p.func = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel_flow<ST, 2>)
-                                 : reinterpret_cast<const void*>(&step_kernel_flow<ST, 3>);
+    // the same choice of paths as the per-step kernels (plan_t)
+    if constexpr (sizeof(typename ST::T) == 2) {
+        p.func = shape.tw == 256 ? reinterpret_cast<const void*>(&step_kernel_flow<ST, 2, true>)
+                                 : reinterpret_cast<const void*>(&step_kernel_flow<ST, 3, true>);
+    } else {
+        p.func = shape.split ? reinterpret_cast<const void*>(&step_kernel_flow<ST, 0, true>)
+                             : reinterpret_cast<const void*>(&step_kernel_flow<ST>);
+    }
     p.block = dim3(shape.tw / cells_per_thread(storage_precision<ST>(), shape.tw), shape.bh);
     p.smem = 0;
     return p;
