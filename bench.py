@@ -449,10 +449,10 @@ LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepp
               sweep_lag=0)
 # the studies (other grid sizes and many small grids): one launch per step
 STUDY_LAUNCH = dict(tile_w=64, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
-# 16-bit storages: 128-cell tile rows, four cells per thread (8-byte vectors);
-# measured ahead of the eight-cell rows (133.7 against 136.4 us per step of
-# the 8192 x 4096 eye) and of cell pairs (142.4 us)
-VEC16_LAUNCH = dict(tile_w=128, block_rows=4, rows_per_thread=2, blocks_per_sm=0, stepping=0)
+# 16-bit storages: 256-cell tile rows, eight cells per thread (16-byte
+# vectors); with the boundary cells in edge-cell chunks they measured ahead of
+# the four-cell rows (104.0 against 110.5 us per step of the 8192 x 4096 eye)
+VEC16_LAUNCH = dict(tile_w=256, block_rows=4, rows_per_thread=1, blocks_per_sm=0, stepping=0)
 
 
 def _time_intervals(dom_or_batch, n, batch=False):
