@@ -377,7 +377,11 @@ lbm_status lbm_vortex(lbm_domain* dom, const double* dev_u, lbm_vortex_info* out
  * caller: lbm_batch_bytes. */
 
 /* Bytes for a batch of up to max_instances members holding max_tiles tiles
- * in total (sum of lbm_get_tile_count of the members at the batch's shape). */
+ * in total (sum of lbm_get_tile_count of the members at the batch's shape).
+ * The per-step list also holds the members' edge-cell chunks (blocks that
+ * update the cells next to a boundary, one per thread), up to max_tiles of
+ * them.  Tiles beyond max_tiles make lbm_batch_add fail, chunks beyond it
+ * the batch's next step, both with LBM_EBUSY. */
 size_t lbm_batch_bytes(int32_t max_instances, int64_t max_tiles);
 
 /* Create an empty batch.  launch (may be NULL) is the shape every member is
