@@ -323,6 +323,14 @@ int64_t lbm_get_step(const lbm_domain* dom);
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_geometry_info* info);
 int64_t lbm_get_tile_count(const lbm_domain* dom);
 
+/* Edge cells of the domain's plain steps at its launch shape: the active
+ * cells that no interior cell pair of the pair or vector path covers, which
+ * separate blocks update one per thread (the 16-bit storages always; FP32
+ * grids when more than 8 % of their active cells lie in 64-cell row segments
+ * next to a boundary).  0 when the rows update every cell themselves (FP64,
+ * other FP32 grids, tiles 32 wide, odd grid widths); -1 for a null domain. */
+int64_t lbm_get_edge_cell_count(const lbm_domain* dom);
+
 /* Bytes of algorithmic HBM traffic of one step of this domain: 2 x 13
  * populations per active cell at the storage precision plus one mask byte per
  * tiled cell. */

@@ -283,7 +283,8 @@ __device__ __forceinline__ void load_cell(const InstDesc& d, const int* nb, type
 template <class ST, bool OBS, int PAR, class A = double>
 __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
                                           const typename ST::R* fin, const typename ST::R* gin,
-                                          uint8_t m, int mode, A* acc) {
+                                          uint8_t m, int mode, A* acc,
+                                          int64_t ntw = -1) {
     using T = typename ST::T;
     using R = typename ST::R;
     using E = Rn<R>;
@@ -353,11 +354,12 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
     }
 
     // neighbour types (only next to a boundary)
+    // (ntw >= 0: the host's word of them, an edge cell's; else read here)
     uint32_t ntypes = 0, bnd = 0;
     if (m & NEAR_BOUNDARY) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const uint32_t tn = d.mask[nb[i]] & TYPE_BITS;
+            const uint32_t tn = ntw >= 0 ? ((uint32_t)ntw >> (4 * (i - 1))) & 15u : d.mask[nb[i]] & TYPE_BITS;
             ntypes |= tn << (4 * (i - 1));
             if (tn > POROUS) bnd |= 1u << i;
         }
@@ -581,14 +583,15 @@ __device__ __forceinline__ void cell_body(const InstDesc& d, int x, int y,
 }
 
 template <class ST, bool OBS, int PAR, class A = double>
-__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode, A* acc) {
+__device__ __forceinline__ void update_cell(const InstDesc& d, int x, int y, int mode, A* acc,
+                                            int64_t ntw = -1) {
     using R = typename ST::R;
     int nb[9];
     neighbours(d, x, y, nb);
     R f[9], g[4];
     uint8_t m;
     load_cell<ST, PAR>(d, nb, f, g, m);
-    cell_body<ST, OBS, PAR, A>(d, x, y, f, g, m, mode, acc);
+    cell_body<ST, OBS, PAR, A>(d, x, y, f, g, m, mode, acc, ntw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1277,7 +1280,7 @@ __device__ __noinline__ void tile_edge_cells(const InstDesc& sd, int li) {
     for (int e = sd.eoff[li] + (int)(threadIdx.y * blockDim.x + threadIdx.x); e < e1; e += nthreads) {
         const int c = sd.edges[e];
         const int y = c / sd.nx;
-        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr);
+        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr, sd.etypes[e]);
     }
 }
 
@@ -1289,7 +1292,7 @@ __device__ __noinline__ void edge_block(const InstDesc& sd, int4 te) {
     if (k < te.w) {
         const int c = sd.edges[te.z + k];
         const int y = c / sd.nx;
-        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr);
+        update_cell<ST, false, PAR, double>(sd, c - y * sd.nx, y, 0, nullptr, sd.etypes[te.z + k]);
     }
 }
 

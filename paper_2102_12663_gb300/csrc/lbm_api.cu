@@ -109,8 +109,8 @@ static size_t real_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct Layout {
     int64_t npad, max_tiles, max_entries;
-    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, fold, edges, eoff,
-        total;
+    size_t desc, obs, mask, tiles, nbr, flags, items, qcol, qtab, partials, usnap, pops, tmap, fold, edges, etypes,
+        eoff, total;
     int64_t max_curved;
 };
 
@@ -152,6 +152,7 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.fold = off; off = align_up(off + ((size_t)FOLD_MAX * NPART + 1) * sizeof(double));
     // edge cells: at most one entry per cell, and per-tile offsets
     L.edges = off; off = align_up(off + (size_t)L.npad * sizeof(int32_t));
+    L.etypes = off; off = align_up(off + (size_t)L.npad * sizeof(uint32_t));
     L.eoff = off; off = align_up(off + (size_t)(L.max_tiles + 1) * sizeof(int32_t));
     L.total = off;
     return true;
@@ -352,6 +353,24 @@ static lbm_status build_tiles(lbm_domain* d) {
         edges.clear();
         std::fill(eoff.begin(), eoff.end(), 0);
     }
+    // each edge cell's neighbour types, as cell_body reads them (links 1..8,
+    // periodic wrap; only for a cell marked next to a boundary)
+    std::vector<uint32_t> etypes(edges.size(), 0u);
+    {
+        static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        for (size_t e = 0; e < edges.size(); ++e) {
+            const int64_t c = edges[e];
+            const int y = (int)(c / d->nx), x = (int)(c - (int64_t)y * d->nx);
+            if (!(d->hmask[c] & NEAR_BOUNDARY)) continue;
+            uint32_t w = 0;
+            for (int i = 1; i < 9; ++i) {
+                const int xn = (x + EX[i] + d->nx) % d->nx, yn = (y + EY[i] + d->ny) % d->ny;
+                w |= (uint32_t)(d->hmask[(int64_t)yn * d->nx + xn] & TYPE_BITS) << (4 * (i - 1));
+            }
+            etypes[e] = w;
+        }
+    }
     eoff[tiles.size()] = (int32_t)edges.size();
     if ((int64_t)edges.size() > d->L.npad) return fail(LBM_EINVAL, "edge list overflow");
     const int per_chunk = (tw / cpt) * d->launch.block_rows;  // threads of a block
@@ -416,6 +435,9 @@ static lbm_status build_tiles(lbm_domain* d) {
     }
     CK(cudaMemcpyAsync(d->base + d->L.eoff, eoff.data(), eoff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                        d->stream));
+    if (!edges.empty())
+        CK(cudaMemcpyAsync(d->base + d->L.etypes, etypes.data(), etypes.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice, d->stream));
     if (!edges.empty())
         CK(cudaMemcpyAsync(d->base + d->L.edges, edges.data(), edges.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, d->stream));
@@ -924,6 +946,7 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     h.partials = reinterpret_cast<double*>(d->base + d->L.partials);
     h.edges = reinterpret_cast<const int32_t*>(d->base + d->L.edges);
     h.eoff = reinterpret_cast<const int32_t*>(d->base + d->L.eoff);
+    h.etypes = reinterpret_cast<const uint32_t*>(d->base + d->L.etypes);
     h.obs = d->d_obs;
     h.npad = d->L.npad;
     h.nx = d->nx;
@@ -1606,6 +1629,8 @@ extern "C" lbm_status lbm_get_info(const lbm_domain* d, lbm_geometry_info* info)
 }
 
 extern "C" int64_t lbm_get_tile_count(const lbm_domain* d) { return d ? d->ntiles : -1; }
+
+extern "C" int64_t lbm_get_edge_cell_count(const lbm_domain* d) { return d ? d->n_edges : -1; }
 
 extern "C" double lbm_step_bytes(const lbm_domain* d) {
     if (!d) return 0.0;

@@ -113,6 +113,10 @@ struct InstDesc {
     // list flagged TILE_EDGE (one cell per thread of a block); the dataflow
     // kernel updates a tile's own after its rows.
     const int32_t* edges;
+    // per edge cell: its eight neighbours' cell types, 4 bits each in link
+    // order (0 for a cell not next to a boundary), as the per-cell update
+    // would read them from the mask
+    const uint32_t* etypes;
     const int32_t* eoff;
     // first tile of this instance in a batch's merged tile list (0 for a
     // domain): the dataflow items carry merged indices, eoff local ones

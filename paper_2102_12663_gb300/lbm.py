@@ -149,6 +149,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "lbm_debug_stall_tile": (i32, [dom, i32]),
         "lbm_get_info": (i32, [dom, P(GeometryInfo)]),
         "lbm_get_tile_count": (i64, [dom]),
+        "lbm_get_edge_cell_count": (i64, [dom]),
         "lbm_step_bytes": (dbl, [dom]),
         "lbm_destroy_domain": (None, [dom]),
         "lbm_batch_bytes": (sz, [i32, i64]),
@@ -417,6 +418,10 @@ class Domain:
 
     def tile_count(self) -> int:
         return int(self._L.lbm_get_tile_count(self._h))
+
+    def edge_cell_count(self) -> int:
+        """Cells that plain steps update in edge-cell blocks (0: none)."""
+        return int(self._L.lbm_get_edge_cell_count(self._h))
 
     def step_bytes(self) -> float:
         return float(self._L.lbm_step_bytes(self._h))

@@ -196,3 +196,58 @@ def test_fp32_check_step_observables_match_the_oracle():
             assert o[k] == pytest.approx(oo[kr], rel=2e-5), k
         assert (o["n_fluid"], o["n_cornea"], o["n_iris"]) == (oo["n_fluid"], oo["n_cornea"], oo["n_iris"])
     b.close()
+
+
+def channel_with_wall(nx=256, ny=128):
+    """Periodic fluid channel with a two-row adiabatic wall across it: only
+    the rows beside the wall hold boundary cells, 2 of 128 rows, below the
+    8 % share from which an FP32 grid takes edge-cell chunks."""
+    m, desc = W.porous_box(nx, ny)
+    m[:, :] = W.FLUID
+    m[ny // 2:ny // 2 + 2, :] = W.ADIABATIC
+    params = dict(tau=0.7, tau_T=0.8, drive=(2e-6, 0.0), K_tm=0.5, noise_amp=1e-3, T0=0.3, T_cold=0.2,
+                  T_hot=0.4, g_beta=1e-4, g_dir=(0.0, -1.0), seed=5)
+    return m, desc, params
+
+
+def test_split_and_unsplit_members_bitwise_and_against_the_oracle():
+    """FP32 members choose edge-cell chunks per grid: a small eye takes them,
+    the walled channel does not.  A batch holding both runs the chunked
+    kernel, where the channel's rows update every cell as they do alone; so
+    each member computes the same bits alone and in the batch, and the
+    channel matches the oracle."""
+    m, desc, params = channel_with_wall()
+    geo = dict(mask=m, **{k: v for k, v in desc.items() if k not in ("nx", "ny")})
+
+    def channel():
+        d = lbm.Domain(geo, precision="f32")
+        d.set_launch(**SHAPE)
+        d.set_params(params)
+        return d
+
+    eye = small_instances(1, seed=3)[0]
+    ch_alone, eye_alone = channel(), make(eye, "f32")
+    assert ch_alone.edge_cell_count() == 0
+    assert eye_alone.edge_cell_count() > 0
+    ch_mix, eye_mix = channel(), make(eye, "f32")
+    b = lbm.Batch("f32", max_instances=2, max_tiles=1 << 16, launch=SHAPE)
+    b.add(ch_mix)
+    b.add(eye_mix)
+    for d in (ch_alone, eye_alone):
+        d.step(57)
+    b.step(57)
+    for a, x in ((ch_alone, ch_mix), (eye_alone, eye_mix)):
+        fa, ga = pops(a)
+        fx, gx = pops(x)
+        assert np.array_equal(fa, fx) and np.array_equal(ga, gx)
+    g = O.mask_geom(desc["nx"], desc["ny"], desc["periodic_x"], desc["periodic_y"], desc["inlet_dir"],
+                    desc["inlet_profile"], desc["inlet_lo"], desc["inlet_width"])
+    ref = O.State(g, O.make_params(**params), m)
+    ref.run(57)
+    f, gg = pops(ch_mix)
+    # the FP32 parity bound of the other tests, max(1e-5, 5e-8 n) of the largest value
+    assert np.abs(f - ref.f).max() <= 1e-5 * np.abs(ref.f).max()
+    assert np.abs(gg - ref.T).max() <= 1e-5 * np.abs(ref.T).max()
+    b.close()
+    for d in (ch_alone, eye_alone):
+        d.close()
