@@ -558,15 +558,27 @@ def run_precision(args):
                 "residual_per_100_steps": float(x[-1, 4])}
         return out
 
-    studies = [study(256, 128, 600_000), study(512, 256, 1_500_000),
-               study(cfg["check_nx"], cfg["check_ny"], args.transient_steps)]
+    big = args.transient_steps
+    if big <= 0:
+        # to steady state: the FP64 path's residual below 1e-7 per 100 steps
+        # (capped), then the sampling window of 20 checks on top
+        dom = lbm.Domain(dict(nx=cfg["check_nx"], ny=cfg["check_ny"], angle_deg=cfg["angle_deg"]), precision="f64")
+        dom.set_params(W.config_params(cfg, ny=cfg["check_ny"]))
+        _, done = dom.run_to_steady(1e-7, check_every=CHECK, max_steps=args.steady_cap)
+        dom.close()
+        big = int(done) + 20 * 2500
+    grids = {"256": (256, 128, 600_000), "512": (512, 256, 1_500_000),
+             "1024": (cfg["check_nx"], cfg["check_ny"], big)}
+    studies = [study(*grids[g]) for g in args.precision_grids.split(",")]
     line = {"metric": "reduced-storage precision study", "unit": "relative error / MLUPS",
             "dtype": "f16/bf16 storage, f32 arithmetic, f64 reductions", "data": "synthetic",
             "config": {"workload": f"throughput: {cfg['nx']}x{cfg['ny']} eye; errors of the observables "
                                    f"against the FP64 path, time-averaged over 20 checks 2,500 steps apart: "
                                    f"steady 256x128 (600k steps) and 512x256 (1.5M steps) eyes, and the "
-                                   f"{cfg['check_nx']}x{cfg['check_ny']} eye at {args.transient_steps} steps "
-                                   f"(temperature field still settling)",
+                                   f"{cfg['check_nx']}x{cfg['check_ny']} eye at {big} steps "
+                                   + ("(temperature field still settling)" if args.transient_steps > 0 else
+                                      "(FP64 residual below 1e-7 per 100 steps, or the cap)")
+                                   + f"; grids run: {args.precision_grids}",
                        "tau": cfg["tau"], "Ra": cfg["Ra"], "K_tm": cfg["K_tm"]},
             "throughput": thr, "peak_gbs": peak, "peak_kind": peak_kind, "errors": studies,
             "oracle_check_steps": args.oracle_steps}
@@ -753,6 +765,11 @@ def main():
     ap.add_argument("--intervals", type=int, default=10, help="timed check intervals (studies)")
     ap.add_argument("--transient-steps", type=int, default=300000,
                     help="steps of the 1024 x 512 equal-step error comparison")
+    ap.add_argument("--steady-cap", type=int, default=6_000_000,
+                    help="precision: step cap of the FP64 run to steady state on the 1024 x 512 eye "
+                         "(--transient-steps 0)")
+    ap.add_argument("--precision-grids", default="256,512,1024",
+                    help="precision: the error studies to run (256 x 128, 512 x 256, 1024 x 512 eyes)")
     ap.add_argument("--oracle-steps", type=int, default=500, help="oracle cross-check steps")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--serve-ny-lo", type=int, default=64, help="serving: smallest NY of a request")
