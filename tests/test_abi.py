@@ -97,9 +97,11 @@ def test_domain_bytes_and_no_gpu_needed_for_sizes(L):
     b16 = L.lbm_domain_bytes(ctypes.byref(g), lbm.F16DEV)
     b64 = L.lbm_domain_bytes(ctypes.byref(g), lbm.F64)
     N = 4096 * 2048
-    # populations (13 x 4 B), velocity snapshot (2 x 4 B), mask (1 B) and an
-    # edge-pass list entry (4 B) per cell, plus per-tile tables (tile list,
-    # partials, neighbour lists, progress words, sweep items, edge offsets)
-    assert 65 * N < b32 < 65 * N + (32 << 20)
+    # populations (13 x 4 B), velocity snapshot (2 x 4 B), mask (1 B), an
+    # edge-cell entry and its neighbour-type word (2 x 4 B) and room for one
+    # edge-cell chunk per 32 cells in the tile list (0.5 B) per cell, plus
+    # per-tile tables (tile list, partials, neighbour lists, progress words,
+    # sweep items, edge offsets)
+    assert 69 * N < b32 < 69 * N + (32 << 20)
     assert b16 < b32 < b64
     assert L.lbm_domain_bytes(ctypes.byref(g), 7) == 0
