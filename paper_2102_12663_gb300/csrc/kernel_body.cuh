@@ -1801,7 +1801,7 @@ __global__ void __launch_bounds__(WS_THREADS, LBM_WS_MINB) step_kernel_ws(const 
 // MB > 0: resident blocks of 256 threads to compile for (a register budget
 // chosen per launch geometry), else the storage's default
 // SPLIT (plain FP32-arithmetic steps): the launch runs the edge-cell chunks
-// that lead the tile list, and the rows update interior pairs only
+// spread among the tiles, and the rows update interior pairs only
 template <class ST, bool OBS, class A = double, int MB = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(256, MB > 0 ? MB : (OBS ? 2 : step_min_blocks<ST>())) step_kernel(const InstDesc* __restrict__ insts,
                                                     const int4* __restrict__ tiles, int ntiles,

@@ -27,12 +27,14 @@ StepPlan step_plan(int precision, int mode, Shape shape) {
     return precision == 0 ? step_plan_f64(mode, shape) : step_plan_lp(precision, mode, shape);
 }
 
-// The entries a plan's kernel runs: a plain FP32-arithmetic step all of them
-// (the edge-cell chunks first), the other kernels the tiles after the chunks.
-// Its grid: one block per entry, or at most cap blocks (cap > 0) looping over them.
+// The entries a plan's kernel runs.  The list holds the ntiles tiles, then
+// the same tiles with the nchunks edge-cell chunks spread evenly among them:
+// a plain step that takes the chunks runs the second part, the other kernels
+// the first.  Its grid: one block per entry, or at most cap blocks (cap > 0)
+// looping over them.
 static void plan_entries(const StepPlan& pl, const int4* all, int nchunks, int ntiles, int cap, const int4** t,
                          int* n, int* grid) {
-    *t = pl.edges ? all : all + nchunks;
+    *t = pl.edges ? all + ntiles : all;
     *n = pl.edges ? nchunks + ntiles : ntiles;
     *grid = std::max(1, cap > 0 ? std::min(cap, *n) : *n);
     if (pl.max_grid > 0) *grid = std::min(*grid, pl.max_grid);
@@ -135,8 +137,9 @@ static bool make_layout(int nx, int ny, int prec, Layout& L) {
     L.desc = off; off = align_up(off + sizeof(InstDesc));
     L.obs = off; off = align_up(off + NOBS * sizeof(double));
     L.mask = off; off = align_up(off + (size_t)L.npad);
-    // tile list: the edge-cell chunks (at most one per 32 cells) and the tiles
-    L.max_entries = L.max_tiles + L.npad / 32 + 1;
+    // tile list: the tiles, then the tiles with the edge-cell chunks (at most
+    // one per 32 cells) spread among them
+    L.max_entries = 2 * L.max_tiles + L.npad / 32 + 1;
     L.tiles = off; off = align_up(off + (size_t)L.max_entries * sizeof(int4));
     L.nbr = off; off = align_up(off + (size_t)L.max_tiles * 8 * sizeof(int));
     L.flags = off; off = align_up(off + (size_t)(L.max_tiles + 2) * sizeof(int));
@@ -190,7 +193,7 @@ struct lbm_domain {
     int ntiles = 0;
     int64_t tiled_cells = 0;
     int64_t n_edges = 0;              // edge cells (plain FP32-arithmetic steps)
-    int nchunks = 0;                  // edge-cell chunks leading d_tiles
+    int nchunks = 0;                  // edge-cell chunks in d_tiles' second part
     int split = 0;                    // plain steps take the edge-cell chunks (Shape::split)
     int64_t active_cells = 0;         // fluid and porous cells
     int64_t slow_cells = 0;           // active cells of row segments that need the per-cell update
@@ -280,6 +283,18 @@ static std::vector<int4> boundary_tiles_first(const std::vector<int4>& tiles) {
 }
 
 // tile list: every tw x th tile holding at least one active cell
+// Appends tiles with chunks spread evenly among them (chunk j before tile
+// j * ntiles / nchunks).
+static void append_interleaved(std::vector<int4>& out, const std::vector<int4>& tiles,
+                               const std::vector<int4>& chunks) {
+    size_t j = 0;
+    for (size_t i = 0; i < tiles.size(); ++i) {
+        while (j < chunks.size() && j * tiles.size() <= i * chunks.size()) out.push_back(chunks[j++]);
+        out.push_back(tiles[i]);
+    }
+    while (j < chunks.size()) out.push_back(chunks[j++]);
+}
+
 static lbm_status build_tiles(lbm_domain* d) {
     const int tw = d->launch.tile_w, th = d->launch.block_rows * d->launch.rows_per_thread;
     const int ntx = (d->nx + tw - 1) / tw, nty = (d->ny + th - 1) / th;
@@ -377,7 +392,7 @@ static lbm_status build_tiles(lbm_domain* d) {
     std::vector<int4> chunks;
     for (size_t e = 0; e < edges.size(); e += (size_t)per_chunk)
         chunks.push_back(make_int4(0, TILE_EDGE, (int)e, (int)std::min<size_t>(per_chunk, edges.size() - e)));
-    if ((int64_t)(chunks.size() + tiles.size()) > d->L.max_entries) return fail(LBM_EINVAL, "tile list overflow");
+    if ((int64_t)(chunks.size() + 2 * tiles.size()) > d->L.max_entries) return fail(LBM_EINVAL, "tile list overflow");
     // neighbour tiles in the order of the links e_1..e_8, wrapping around
     // periodic edges only (no active cell lies on a non-periodic edge, so no
     // link crosses one)
@@ -420,11 +435,13 @@ static lbm_status build_tiles(lbm_domain* d) {
     d->tiled_cells = cells;
     d->h.ntiles = d->ntiles;
     d->htiles = tiles;
-    // per-step launch order: the edge-cell chunks, then the tiles, boundary
-    // tiles first (the longer blocks start early)
-    std::vector<int4> launch_order = chunks;
+    // per-step launch order: the tiles, boundary tiles first (the longer
+    // blocks start early); then the same with the edge-cell chunks spread
+    // evenly among them, so that every SM mixes their latency-bound
+    // per-cell work with streaming tiles
     const std::vector<int4> tile_order = boundary_tiles_first(tiles);
-    launch_order.insert(launch_order.end(), tile_order.begin(), tile_order.end());
+    std::vector<int4> launch_order = tile_order;
+    append_interleaved(launch_order, tile_order, chunks);
     if (!tiles.empty()) {
         CK(cudaMemcpyAsync(d->d_tiles, launch_order.data(), launch_order.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, d->stream));
@@ -1704,7 +1721,7 @@ struct lbm_batch {
     std::vector<double> hobs;
     lbm_launch launch{128, 1, 2, 0, LBM_STEP_PER_LAUNCH, 1, 0};
     int ntiles = 0;
-    int nchunks = 0;  // edge-cell chunks leading d_tiles
+    int nchunks = 0;  // edge-cell chunks in d_tiles' second part
     int split = 0;    // plain steps take the edge-cell chunks (Shape::split)
     bool dirty = true;
     // per-step launches take the tiles holding boundary cells (the slower
@@ -1722,8 +1739,9 @@ static BatchLayout batch_layout(int max_inst, int64_t max_tiles) {
     size_t off = 0;
     L.table = off; off = align_up(off + (size_t)max_inst * sizeof(InstDesc));
     L.obs = off; off = align_up(off + (size_t)max_inst * NOBS * sizeof(double));
-    // per-step list: the tiles and up to as many edge-cell chunks
-    L.tiles = off; off = align_up(off + (size_t)2 * max_tiles * sizeof(int4));
+    // per-step list: the tiles, then the tiles with up to as many edge-cell
+    // chunks spread among them
+    L.tiles = off; off = align_up(off + (size_t)3 * max_tiles * sizeof(int4));
     L.nbr = off; off = align_up(off + (size_t)max_tiles * 8 * sizeof(int));
     L.flags = off; off = align_up(off + (size_t)(max_tiles + 2) * sizeof(int));
     L.items = off; off = align_up(off + (size_t)max_tiles * sizeof(int4));
@@ -1847,11 +1865,12 @@ static lbm_status batch_rebuild(lbm_batch* b) {
     // keeps its own choice, so it computes the same alone and in the batch)
     b->split = 0;
     for (const lbm_domain* m : b->members) b->split |= m->split;
-    if ((int64_t)(chunks.size() + tiles.size()) > 2 * b->max_tiles)
+    if ((int64_t)chunks.size() > b->max_tiles)
         return fail(LBM_EBUSY, "batch tile capacity exceeded (edge-cell chunks)");
-    // per-step list: the members' edge-cell chunks, then the tiles
-    std::vector<int4> order = chunks;
-    order.insert(order.end(), tiles.begin(), tiles.end());
+    // per-step list: the tiles, then the tiles with the members' edge-cell
+    // chunks spread among them
+    std::vector<int4> order = tiles;
+    append_interleaved(order, tiles, chunks);
     if (!tiles.empty()) {
         CK(cudaMemcpyAsync(b->d_tiles, order.data(), order.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            b->stream));

@@ -144,8 +144,8 @@ __host__ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDes
 constexpr int TILE_PURE = 1 << 30;
 // an edge-cell chunk {instance, TILE_EDGE, first, count}: cells edges[first ..
 // first + count) of the instance, one per thread, in plain steps of the
-// FP32-arithmetic kernels (the chunks lead the tile list; the other kernels
-// are launched on the tiles after them)
+// FP32-arithmetic kernels (spread among the tiles in a second part of the
+// tile list; the other kernels are launched on the first part, the tiles alone)
 constexpr int TILE_EDGE = 1 << 29;
 constexpr int TILE_INDEX = TILE_EDGE - 1;
 
@@ -423,7 +423,7 @@ struct StepPlan {
     dim3 block;
     size_t smem;
     int max_grid = 0;  // persistent kernels: co-resident blocks on the device (0: no cap)
-    bool edges = false;  // runs the edge-cell chunks that lead the tile list
+    bool edges = false;  // runs the tile list's second part, tiles and edge-cell chunks
 };
 // mode: the step's observation mode (0 for a plain step)
 StepPlan step_plan(int precision, int mode, Shape shape);
