@@ -930,9 +930,9 @@ extern "C" lbm_status lbm_create_domain(const lbm_geometry_desc* desc, int32_t p
     }
     mark_near_boundary(d->hmask.data(), d->nx, d->ny);
     if (!dev_buf || bytes < d->L.total || (reinterpret_cast<uintptr_t>(dev_buf) % ALIGN) != 0) {
+        const size_t need = d->L.total;
         delete d;
-        return fail(LBM_ENOMEM, "device buffer too small or not 256-byte aligned (need %zu bytes)",
-                    d->L.total);
+        return fail(LBM_ENOMEM, "device buffer too small or not 256-byte aligned (need %zu bytes)", need);
     }
     d->stream = static_cast<cudaStream_t>(stream);
     d->base = static_cast<char*>(dev_buf);
@@ -2055,15 +2055,16 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_candidate, 
     if (steps_per_candidate < 2) return fail(LBM_EINVAL, "steps_per_candidate must be >= 2");
     if (b->members.empty()) return fail(LBM_EINVAL, "empty batch");
     // one launch per step on most shapes, dataflow stepping on the ones that suit it
+    // (sweep_steps 0, sweep_lag 0: one step per sweep, the default lag)
     static const lbm_launch cand[] = {
-        {128, 2, 2, 0, LBM_STEP_PER_LAUNCH}, {64, 2, 2, 0, LBM_STEP_PER_LAUNCH},
-        {64, 4, 1, 0, LBM_STEP_PER_LAUNCH},  {64, 4, 2, 0, LBM_STEP_PER_LAUNCH},
-        {128, 1, 4, 0, LBM_STEP_PER_LAUNCH}, {128, 1, 8, 0, LBM_STEP_PER_LAUNCH},
-        {256, 1, 8, 0, LBM_STEP_PER_LAUNCH}, {64, 4, 2, 0, LBM_STEP_FLOW},
-        {64, 4, 3, 0, LBM_STEP_FLOW},        {128, 2, 2, 0, LBM_STEP_FLOW},
+        {128, 2, 2, 0, LBM_STEP_PER_LAUNCH, 0, 0}, {64, 2, 2, 0, LBM_STEP_PER_LAUNCH, 0, 0},
+        {64, 4, 1, 0, LBM_STEP_PER_LAUNCH, 0, 0},  {64, 4, 2, 0, LBM_STEP_PER_LAUNCH, 0, 0},
+        {128, 1, 4, 0, LBM_STEP_PER_LAUNCH, 0, 0}, {128, 1, 8, 0, LBM_STEP_PER_LAUNCH, 0, 0},
+        {256, 1, 8, 0, LBM_STEP_PER_LAUNCH, 0, 0}, {64, 4, 2, 0, LBM_STEP_FLOW, 0, 0},
+        {64, 4, 3, 0, LBM_STEP_FLOW, 0, 0},        {128, 2, 2, 0, LBM_STEP_FLOW, 0, 0},
         // 16-bit storages only: eight cells per thread on 256-cell rows
-        {256, 4, 1, 0, LBM_STEP_PER_LAUNCH}, {256, 4, 2, 0, LBM_STEP_PER_LAUNCH},
-        {256, 8, 1, 0, LBM_STEP_PER_LAUNCH}, {256, 4, 2, 0, LBM_STEP_FLOW}};
+        {256, 4, 1, 0, LBM_STEP_PER_LAUNCH, 0, 0}, {256, 4, 2, 0, LBM_STEP_PER_LAUNCH, 0, 0},
+        {256, 8, 1, 0, LBM_STEP_PER_LAUNCH, 0, 0}, {256, 4, 2, 0, LBM_STEP_FLOW, 0, 0}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
