@@ -384,8 +384,9 @@ def cpu_model() -> str:
 def side_studies(dev) -> dict:
     """Short measurements of the other forms, reported beside the headline
     (they do not enter `value`): 16-bit deviation storage on the 8192 x 4096
-    eye (three check intervals per storage, eight-cell tile rows) and the
-    64-instance FP32 batch (three check intervals).  A few seconds."""
+    eye (three check intervals per storage, eight-cell tile rows), the
+    64-instance FP32 batch (three check intervals) and 24 served requests
+    against the one-at-a-time loop.  About 15 seconds."""
     import torch
 
     from paper_2102_12663_gb300 import lbm
@@ -439,7 +440,33 @@ def side_studies(dev) -> dict:
     for d in doms:
         d.close()
     torch.cuda.empty_cache()
+    out["serve_24"] = serve_study(24)
     return out
+
+
+def serve_study(n):
+    """The serving workload's throughput part on n requests (Poisson at 20/s,
+    NY 64..256, half FP16 refined to the FP32 criterion): continuous batching
+    against the one-at-a-time FP32 loop (`--workload serve` adds the accuracy
+    sample against FP64)."""
+    from paper_2102_12663_gb300 import serve
+    from paper_2102_12663_gb300 import workloads as W
+    draws = W.request_stream(n, rate_hz=20.0, ny_lo=64, ny_hi=256, fp16_share=0.5)
+    reqs = serve.requests_from_draws(draws, tol_by_precision=W.SERVE_TOL, cap_efolds=20.0)
+    srv = serve.Server(budget_bytes=150e9, tol=1e-7, check_every=CHECK, max_steps=10**9,
+                       launch=STUDY_LAUNCH, refine_tol={"f16": W.SERVE_TOL["f32"]})
+    res = srv.run(reqs, realtime=True)
+    s_served = serve.summary(res, srv.wall_s)
+    srv.close()
+    base_reqs = serve.requests_from_draws(draws, tol_by_precision={"f32": W.SERVE_TOL["f32"],
+                                                                   "f16": W.SERVE_TOL["f32"]},
+                                          cap_efolds=20.0)
+    base = serve.solve_one_at_a_time(base_reqs, check_every=CHECK, launch=STUDY_LAUNCH, realtime=True)
+    s_base = serve.summary(base, max(r.finish_s for r in base))
+    keep = ("solves_per_s", "p50_s", "p99_s", "converged", "capped")
+    return {"served": {k: s_served[k] for k in keep},
+            "one_at_a_time_fp32": {k: s_base[k] for k in keep},
+            "speedup_solves_per_s": s_served["solves_per_s"] / s_base["solves_per_s"]}
 
 
 # the FP32 4096 x 2048 line: 64 x 4 tiles, one graph-replayed launch per step
