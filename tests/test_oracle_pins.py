@@ -569,3 +569,74 @@ def test_thermal_inlet_and_outlet_rules_through_flow():
     assert np.abs(T[act] - 0.7).max() < 1e-12
     assert np.abs(u[0][act] - 0.02).max() < 1e-12
     assert np.abs(p[act]).max() < 1e-12
+
+
+def _sector_mask(nx, ny, xc, yc, r, deg_lo, deg_hi):
+    """Fluid box with cold cells beyond radius r of (xc, yc) inside the
+    angular sector [deg_lo, deg_hi]: a curved wall whose angles have no
+    symmetry axis; the cold wall's normal is radial from (xc, yc)."""
+    m = np.full((ny, nx), W.FLUID, dtype=np.uint8)
+    for y in range(ny):
+        for x in range(nx):
+            th = math.degrees(math.atan2(y - yc, x - xc))
+            if math.hypot(x - xc, y - yc) > r and deg_lo <= th <= deg_hi:
+                m[y, x] = W.COLD
+    g = O.mask_geom(nx, ny, arc=(xc, yc, r))
+    g.eye_normals = 1
+    return m, g
+
+
+@pytest.mark.parametrize("geometry", ["eye", "sector"])
+def test_curved_wall_shear_normal_closed_form(geometry):
+    """Wall shear on the analytic eye's curved cornea and on the iris.  Every
+    active cell holds f = feq(0, 0) + w_i 4.5 (e_i e_i - I/3) : Pi with a
+    uniform traceless Pi = [[-q, s], [s, q]]: then sum_i e_i e_i (f_i - feq_i)
+    = Pi, and p = 0, u = 0.  For a wall of unit normal n at angle theta the
+    shear t.sigma.n with sigma = -(1 - 1/(2 tau)) Pi is, by the double-angle
+    identities, (1 - 1/(2 tau)) |q sin 2 theta + s cos 2 theta|.  The cornea's
+    normal points from the arc's centre to the cell, so each adjacent fluid
+    cell contributes at its own angle; the iris's normal is +y (theta = 90
+    deg), so every iris cell contributes (1 - 1/(2 tau)) |s|.  q and s both
+    non-zero tell a normal from its mirror image (components swapped) on the
+    sector, whose angles (10 to 50 deg) have no symmetry axis; on the eye the
+    cornea is symmetric about its axis, which hides that mirror but not a
+    wrong centre or length."""
+    tau = 0.8
+    if geometry == "eye":
+        nx, ny = 160, 80
+        m, g = O.eye_mask(nx, ny, 45.0)
+    else:
+        nx, ny = 96, 96
+        m, g = _sector_mask(nx, ny, 20.5, 15.5, 40.0, 10.0, 50.0)
+    st = O.State(g, O.make_params(tau=tau), m)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    q, s = 3e-4, 5e-4
+    pxx, pxy, pyy = -q, s, q
+    fneq = 4.5 * w * ((EX * EX - 1 / 3) * pxx + 2 * EX * EY * pxy + (EY * EY - 1 / 3) * pyy)
+    f9 = O.feq(0.0, 0.0, 0.0) + fneq
+    mask = m.reshape(-1)
+    act = mask <= W.POROUS
+    st.f[:, act] = f9[:, None]
+    obs = st.observe()
+
+    k = 1.0 - 1.0 / (2.0 * tau)
+    grid = m.reshape(ny, nx)
+    cornea, iris = [], []
+    for y in range(ny):
+        for x in range(nx):
+            if grid[y, x] != W.FLUID:
+                continue
+            nb = [grid[y + dy, x + dx] for dx in (-1, 0, 1) for dy in (-1, 0, 1)
+                  if (dx or dy) and 0 <= x + dx < nx and 0 <= y + dy < ny]
+            if W.COLD in nb:
+                th = math.atan2(y - g.arc_yc, x - g.arc_xc)
+                cornea.append(k * abs(q * math.sin(2 * th) + s * math.cos(2 * th)))
+            if W.HOT in nb:
+                iris.append(k * abs(s))
+    assert len(cornea) > 20 and (len(iris) > 20 or geometry == "sector")
+    assert obs["n_cornea"] == len(cornea) and obs["n_iris"] == len(iris)
+    assert obs["wss_cornea"] == pytest.approx(np.mean(cornea), rel=1e-12)
+    if iris:
+        assert obs["wss_iris"] == pytest.approx(np.mean(iris), rel=1e-12)
+    # the state is at rest: the other observables see no flow
+    assert obs["peak"] == pytest.approx(0.0, abs=1e-15)
