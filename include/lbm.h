@@ -186,10 +186,14 @@ typedef struct lbm_observables {
 /* Launch shape of the fused step kernel: tiles of tile_w x (block_rows *
  * rows_per_thread) cells, one thread per column (FP64) or column pair (other
  * storages) and row group.  tile_w in {32, 64, 128, 256}, tile_w * block_rows
- * <= 256, tile area >= 128 cells.  The 16-bit storages with tile_w 256 take
- * eight columns per thread instead (32 threads per row, block_rows <= 8):
- * rows whose cells are all away from boundaries then move each population
- * plane as one 16-byte vector of eight cells.
+ * <= 256, tile area >= 128 cells.  The 16-bit storages with tile_w 256 or
+ * 128 take eight or four columns per thread instead (32 threads per row,
+ * block_rows <= 8): rows whose cells are all away from boundaries then move
+ * each population plane as one 16- or 8-byte vector.  Plain steps of the
+ * 16-bit storages, and of FP32 grids with many cells in row segments next
+ * to a boundary, update those cells in separate blocks, one per thread
+ * (lbm_get_edge_cell_count); tiles 256 x 4 measured fastest for the 16-bit
+ * storages, 64 x 4 for FP32.
  *
  * stepping selects how lbm_step advances a domain (the zero default is one
  * launch per step; the dataflow launch is faster where the per-step launch
