@@ -104,15 +104,17 @@ def _sampled(nx, ny, prec, steps, nsamp, every, launch):
     return np.array(out)
 
 
-def test_fp16_steady_observables_within_1e3_of_fp64():
+@pytest.mark.parametrize("nx,ny,steps", [(256, 128, 600_000), (512, 256, 1_500_000)])
+def test_fp16_steady_observables_within_1e3_of_fp64(nx, ny, steps):
     """FP16 deviation storage (FP16 flow populations, companded 16-bit
-    fixed-point heat) on the 256 x 128 eye of the precision workload (tau 0.6,
-    Ra 1e5, K 0.5), eight-cell vector path: IOP, peak speed and both wall
-    shear stresses within 1e-3 of the FP64 path.  Re-rounding every population
-    each step keeps a 16-bit state moving (its residual stays near 3e-6 per
-    100 steps), so the observables are compared over 20 checks 2,500 steps
-    apart: their mean and every single check."""
-    nx, ny, steps, nsamp, every = 256, 128, 600_000, 20, 2500
+    fixed-point heat) on the 256 x 128 and 512 x 256 eyes of the precision
+    workload (tau 0.6, Ra 1e5, K 0.5), eight-cell vector path with edge-cell
+    chunks: IOP, peak speed and both wall shear stresses within 1e-3 of the
+    FP64 path at steady state.  Re-rounding every population each step keeps a
+    16-bit state moving (its residual stays near 3e-6 per 100 steps), so the
+    observables are compared over 20 checks 2,500 steps apart: their mean and
+    every single check."""
+    nsamp, every = 20, 2500
     launch = dict(tile_w=256, block_rows=4, rows_per_thread=1)
     ref = _sampled(nx, ny, "f64", steps, nsamp, every, dict(tile_w=64, block_rows=4, rows_per_thread=1))
     got = _sampled(nx, ny, "f16", steps, nsamp, every, launch)
